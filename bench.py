@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 FFTCWT in scale-samples/s.
+
+Default workload: one N = 2^20 float32 lognormal density field, Morlet wavelet
+(omega0 = 6) at 64 log-spaced scales, periodic AND zero boundary (zero padding
+to M = 2^21), each with the fused wavelet power spectrum.  One step = both
+transforms.  Inputs are resident in HBM when the timed region starts; the L2
+is flushed (a 512 MiB write) between timed steps, outside the timed events.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (a bounded sample of the same workload per step).
+Multi-GPU (torchrun): every rank transforms its own signal; no collective is
+on the data path (weak scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "CWT scale-samples/s"
+UNIT = "scale-samples/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lognormal_n1m_morlet_s64", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if one exists for
+    this kernel class and workload (profiles/traffic.txt: kernel workload bytes)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+                return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(name, budget_s, steps=1, warmup=0):
+    """The FP64 oracle (FFT tier) on the host cores over a bounded sample of the
+    workload: the first scales of each boundary, sized to about budget_s."""
+    import oracle
+    oracle.build()
+    w = synth.WORKLOADS[name]
+    f = synth.workload_signal(name).astype(np.float32).astype(np.float64)
+    sc = synth.workload_scales(name)
+    N = len(f)
+    cores = os.cpu_count() or 1
+    # calibrate on one scale per boundary
+    t0 = time.perf_counter()
+    for b in w["boundaries"]:
+        M = N if b == "periodic" else 1 << int(np.ceil(np.log2(2 * N)))
+        oracle.cwt_fft(f, sc[:1], w["wavelet"], M=M, nthreads=cores)
+    per_scale = time.perf_counter() - t0
+    # OpenMP runs the scales in parallel: a batch of `cores` scales costs about one scale
+    n_batches = max(1, int(budget_s / max(per_scale, 1e-3)))
+    n_sub = int(min(len(sc), n_batches * cores))
+    pick = sc[np.linspace(0, len(sc) - 1, n_sub).astype(int)]
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        for b in w["boundaries"]:
+            M = N if b == "periodic" else 1 << int(np.ceil(np.log2(2 * N)))
+            oracle.cwt_fft(f, pick, w["wavelet"], M=M, nthreads=cores)
+        if it >= warmup:
+            times.append(time.perf_counter() - t0)
+    units = n_sub * N * len(w["boundaries"])
+    t = float(np.mean(times))
+    return {"value": units / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_sub} of {len(sc)} scales (evenly spread) x {len(w['boundaries'])} boundaries, "
+                      f"N={N}, FP64 FFT tier, OpenMP over scales; {t:.1f} s per sample",
+            "seconds": t}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[args.workload]
+    cb = cpu_baseline(args.workload, args.cpu_seconds / 3.0, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["seconds"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": w["n"], "n_scales": w["n_scales"],
+                   "wavelet": w["wavelet"], "boundaries": list(w["boundaries"]),
+                   "sample": cb["sample"]},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2302_03909_gb300 as cwt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    w = synth.WORKLOADS[args.workload]
+    f = synth.workload_signal(args.workload)
+    if world > 1:
+        f = synth.lognormal_field(w["n"], seed=synth.BASE_SEED + 100 + rank) \
+            if "lognormal" in args.workload else synth.multitone(w["n"], seed=synth.BASE_SEED + 100 + rank)
+    sc = synth.workload_scales(args.workload)
+    N, S = len(f), len(sc)
+    plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b) for b in w["boundaries"]]
+    sig = torch.tensor(f, dtype=torch.float32, device=dev)
+    outs = [(p.empty_output(dev), torch.empty(S, dtype=torch.float64, device=dev)) for p in plans]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for p, (W, sp) in zip(plans, outs):
+            cwt.cwt_exec_with_power(p, sig, W, sp, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    for p in plans:
+        cwt.cwt_plan_set_timing(p, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # per-kernel-class device time over the timed region
+    cls_tot = {}
+    for p in plans:
+        for name, (ms, n, b) in cwt.cwt_plan_get_timing(p).items():
+            a = cls_tot.setdefault(name, [0.0, 0, 0.0])
+            a[0] += ms
+            a[1] += n
+            a[2] += b
+    launches = int(sum(v[1] for v in cls_tot.values()))
+    for p in plans:
+        cwt.cwt_plan_set_timing(p, False)
+    dom = max(cls_tot, key=lambda k: cls_tot[k][0])
+    peak, peak_src = load_peaks()
+    achieved = cls_tot[dom][2] / (cls_tot[dom][0] * 1e-3) / 1e9 if cls_tot[dom][0] > 0 else 0.0
+    traffic = load_traffic(dom, args.workload)
+    units_per_step = S * N * len(plans)
+    value = world * units_per_step * args.steps / (total_ms * 1e-3)
+
+    # end to end through the host-buffer entry point: H2D of the signal, D2H of W and spectrum
+    e2e = None
+    if not args.no_e2e:
+        sig_h = torch.tensor(f, dtype=torch.float32).pin_memory()
+        Wh = [torch.empty(p.out_shape, dtype=(torch.complex64 if p.is_complex else torch.float32)).pin_memory()
+              for p in plans]
+        sh = [torch.empty(S, dtype=torch.float64).pin_memory() for _ in plans]
+        for p, W_, s_ in zip(plans, Wh, sh):
+            cwt.cwt_exec_host(p, sig_h, W_, s_, stream)
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for p, W_, s_ in zip(plans, Wh, sh):
+                cwt.cwt_exec_host(p, sig_h, W_, s_, stream)
+        te = time.perf_counter() - t0
+        h2d = sum(N * 4 for _ in plans)
+        d2h = sum(W_.numel() * W_.element_size() + S * 8 for W_ in Wh)
+        e2e = {"value": world * units_per_step * e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": te * 1e3 / e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.workload, args.cpu_seconds)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "n_scales": S, "wavelet": w["wavelet"],
+                       "omega0": 6.0, "boundaries": list(w["boundaries"]),
+                       "fft_len": [p.M for p in plans], "power_spectrum": True,
+                       "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "inputs": "resident in HBM", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": cls_tot[dom][2] / max(1, cls_tot[dom][1]),
+                         "ms_per_launch": cls_tot[dom][0] / max(1, cls_tot[dom][1])},
+            "kernel_classes": {k: {"ms": v[0] / args.steps, "launches": v[1] // args.steps,
+                                   "GBps": (v[2] / (v[0] * 1e-3) / 1e9) if v[0] > 0 else 0.0}
+                               for k, v in cls_tot.items() if v[1] > 0},
+            "hbm_frac_whole_step": (sum(v[2] for v in cls_tot.values()) / (total_ms * 1e-3) / 1e9) / peak,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * cwt.h — C ABI of the GB300 (sm_103a) FFT-based continuous wavelet transform.
+ *
+ * The library computes the FFTCWT of Wang & He, "Comparisons between fast
+ * algorithms for the continuous wavelet transform and applications in
+ * cosmology: the 1D case" (RASTI 2023, arXiv:2302.03909), Sec. 3.1:
+ *
+ *   F(m)   = sum_n f(n) e^{+2 pi i m n / M}                       (Eq. 8, up to L/M)
+ *   W(s,n) = sqrt(dx / w~_s) / M * sum_m F(m) psi_hat(2 pi m~ / (M w~_s)) e^{-2 pi i m n / M}
+ *                                                                  (Eqs. 9-10)
+ *
+ * for n < N, one row per scale, where m~ is the signed frequency in
+ * (-M/2, M/2] and psi_hat is the analytic Fourier transform of the mother
+ * wavelet (Table 2).  M = N for the periodic boundary; for the zero boundary
+ * (Sec. 4.1) the signal is zero-extended to M >= 2N and the first N outputs are
+ * kept.  The global wavelet power spectrum is Eq. 42:
+ *   P(s) = (1/N) sum_{n<N} |W(s,n)|^2.
+ *
+ * Conventions shared by every entry point:
+ *   - Functions return a cwt_status; nothing throws across the ABI.  Arguments
+ *     are checked on the host before any launch.
+ *   - "device pointer" means memory of the CUDA device that was current when
+ *     the plan was created (cudaMalloc, torch tensors, ...).  The caller owns
+ *     every pointer it passes; the plan owns its own workspace and tables.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device entry points are asynchronous on that stream.  A plan's
+ *     workspace is shared by its calls, so one plan must not run on two
+ *     streams at the same time.
+ *   - The device for every call must be the one current at plan creation
+ *     (CWT_ERR_INVALID_ARG otherwise).
+ */
+#ifndef CWT_GB300_H
+#define CWT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cwt_plan cwt_plan; /* opaque; created and destroyed by the library */
+
+typedef enum {
+    CWT_OK = 0,
+    CWT_ERR_INVALID_ARG = 1,  /* bad size, pointer, alignment, scale or option */
+    CWT_ERR_UNSUPPORTED = 2,  /* valid request outside what this build handles */
+    CWT_ERR_OOM = 3,          /* device or host allocation failed */
+    CWT_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+    CWT_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+    CWT_ERR_INTERNAL = 6
+} cwt_status;
+
+/* Mother wavelets of Table 2. */
+typedef enum {
+    CWT_WAVELET_GDW = 0,     /* Gaussian-derived ("Mexican-hat type"):
+                                psi(x) = C_N (2 - x^2) e^{-x^2/4},
+                                psi_hat(k) = 8 sqrt(pi) C_N k^2 e^{-k^2}, C_N = (18 pi)^{-1/4} */
+    CWT_WAVELET_MORLET = 1   /* psi(x) = C_N (e^{-i w0 x} - e^{-w0^2/2}) e^{-x^2/2},
+                                psi_hat(k) = sqrt(2 pi) C_N (e^{-(k-w0)^2/2} - e^{-(k^2+w0^2)/2}),
+                                C_N = pi^{-1/4} (1 - 2 e^{-3 w0^2/4} + e^{-w0^2})^{-1/2};
+                                Table 2 prints w0 = 4, the default here is w0 = 6 */
+} cwt_wavelet;
+
+typedef enum {
+    CWT_BOUNDARY_PERIODIC = 0, /* M = N; N must be a power of two in this build */
+    CWT_BOUNDARY_ZERO = 1      /* zero padding to M = next power of two >= 2N (Eq. 40 context) */
+} cwt_boundary;
+
+typedef enum {
+    CWT_SCALE_DILATION = 0,  /* scales[] are dilations s in samples: w~ = 1 / s */
+    CWT_SCALE_W_TILDE = 1    /* scales[] are the paper's dimensionless w~ = w dx (Eq. 4) */
+} cwt_scale_unit;
+
+typedef enum { CWT_INPUT_F32 = 0, CWT_INPUT_F64 = 1 } cwt_input_dtype;
+
+/* Plan options.  Fill with cwt_plan_opts_default() and change fields. */
+typedef struct {
+    double omega0;       /* Morlet centre wavenumber (default 6) */
+    double dx;           /* sampling interval; W scales with sqrt(dx) (Eq. 4). Default 1 */
+    int32_t scale_unit;  /* cwt_scale_unit (default CWT_SCALE_DILATION) */
+    int32_t input_dtype; /* cwt_input_dtype of the signal (default CWT_INPUT_F32); f64 is
+                            converted to f32 on load */
+    int64_t fft_len;     /* 0: default M.  Zero boundary: any power of two >= N (e.g. the
+                            paper's padding N + 2 Nint(chi / w~_min), rounded up). */
+    double eps_trunc;    /* spectral bins where |psi_hat| < eps_trunc * max|psi_hat| are
+                            skipped (default 1e-10; 0 keeps every bin) */
+} cwt_plan_opts;
+
+void cwt_plan_opts_default(cwt_plan_opts* opts);
+
+/* Plan the transform of N-sample signals at n_scales scales (Sec. 3.1).
+ * scales: host array of n_scales finite values > 0 (copied).  Precomputes the
+ * band of each scale, FP64-generated twiddle tables (stored FP32) and the
+ * workspace on the current device.  *plan is NULL on failure. */
+cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales,
+                           int32_t wavelet, int32_t boundary);
+cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales,
+                              int32_t n_scales, int32_t wavelet, int32_t boundary,
+                              const cwt_plan_opts* opts);
+/* Frees the plan and its device memory (synchronises the device first).  NULL is OK. */
+cwt_status cwt_plan_destroy(cwt_plan* plan);
+
+/* M, the plan's device workspace in bytes, and whether W is complex
+ * (1: interleaved complex64, Morlet; 0: float32, GDW).  Any out-pointer may be NULL. */
+cwt_status cwt_plan_info(const cwt_plan* plan, int64_t* fft_len, size_t* workspace_bytes,
+                         int32_t* out_is_complex);
+
+/* W = CWT of one signal (Eqs. 8-10).
+ * signal_dev: N contiguous f32 (or f64 with CWT_INPUT_F64), device, >= 4 (8) B aligned.
+ * W_dev: [n_scales][N] row-major, device; f32 for the GDW, interleaved complex64
+ *        (re, im) for the Morlet; 4 B (GDW) or 8 B (Morlet) aligned.
+ * Row s holds scale scales[s]. */
+cwt_status cwt_exec(cwt_plan* plan, const void* signal_dev, void* W_dev, void* stream);
+
+/* cwt_exec plus the global wavelet power spectrum (Eq. 42) computed from the
+ * FP32 results before they are stored: spectrum_dev[s] = (1/N) sum_n |W(s,n)|^2,
+ * float64, device, n_scales entries.  Partial sums are reduced in a fixed order,
+ * so repeated calls give bit-identical spectra. */
+cwt_status cwt_exec_with_power(cwt_plan* plan, const void* signal_dev, void* W_dev,
+                               double* spectrum_dev, void* stream);
+
+/* Eq. 42 from a W array already in device memory (layout as cwt_exec writes it):
+ * one read of W, fixed-order reduction, float64 output (device). */
+cwt_status cwt_wavelet_power(cwt_plan* plan, const void* W_dev, double* spectrum_dev,
+                             void* stream);
+
+/* Host-buffer form of cwt_exec_with_power: copies the signal from host memory,
+ * runs the transform in plan-owned device buffers (allocated on first use) and
+ * copies W and, if spectrum_host is not NULL, the spectrum back.  Pinned host
+ * memory gives the fastest copies.  Returns after the results are on the host. */
+cwt_status cwt_exec_host(cwt_plan* plan, const void* signal_host, void* W_host,
+                         double* spectrum_host, void* stream);
+
+/* The paper's scale grid (Sec. 3.1): w~ = w~_min 2^{i + j/n_subs} with
+ * w~_min = c_w pi / N and i < N_levs = Nint(log2 N), written as w~ values in
+ * ascending order.  c_w = 2/sqrt(5) (GDW) or 2 / (w0 + sqrt(w0^2 + 2)) (Morlet).
+ * *n_out receives N_levs * n_subs; w_tilde_out may be NULL to query the count. */
+cwt_status cwt_scales_paper_grid(int64_t N, int32_t wavelet, double omega0, int32_t n_subs,
+                                 double* w_tilde_out, int32_t* n_out);
+
+/* Kernel classes for the timing hook below. */
+typedef enum {
+    CWT_KCLASS_FORWARD = 0, /* forward transform of the signal (Eq. 8) */
+    CWT_KCLASS_BAND = 1,    /* single-pass band kernels: spectrum product (Eq. 10), inverse DFT
+                               (Eq. 9), crop, store and power partials */
+    CWT_KCLASS_WIDE1 = 2,   /* first pass of wide-band scales (spectrum product + A-point DFTs) */
+    CWT_KCLASS_WIDE2 = 3,   /* second pass of wide-band scales (B-point DFTs, crop, store) */
+    CWT_KCLASS_POWER = 4,   /* power-spectrum reductions (Eq. 42) */
+    CWT_KCLASS_COUNT = 5
+} cwt_kernel_class;
+
+/* Timing hook.  enable != 0 makes the following device calls of this plan
+ * record a CUDA event pair around every kernel launch on the call's stream;
+ * any call resets the totals.  Costs one event record per launch boundary. */
+cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable);
+
+/* Totals since cwt_plan_set_timing for one cwt_kernel_class: summed launch
+ * durations in ms, the number of launches, and the algorithmic bytes those
+ * launches must move (signal read and spectrum write for the forward pass;
+ * the W rows written and the spectrum band read for the inverse passes).
+ * Waits for the recorded events.  Any out-pointer may be NULL. */
+cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t kernel_class, double* total_ms, int64_t* launches,
+                               double* algorithmic_bytes);
+
+/* Static description of a status code. */
+const char* cwt_status_string(cwt_status status);
+
+/* Text of the last error a plan recorded (never NULL). */
+const char* cwt_plan_last_error(const cwt_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CWT_GB300_H */

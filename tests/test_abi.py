@@ -1,0 +1,90 @@
+"""CPU checks of the C ABI boundary: the library builds, loads, exports every
+function include/cwt.h declares, and validates arguments on the host before
+touching a device.  No transform is computed here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cwt():
+    import paper_2302_03909_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "cwt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cwt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for required in ["cwt_plan_create", "cwt_exec", "cwt_wavelet_power", "cwt_plan_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(cwt):
+    lib = cwt.load_library()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(cwt.ABI_FUNCTIONS) == declared_functions()
+
+
+def test_status_strings(cwt):
+    assert cwt.cwt_status_string(0) == "ok"
+    assert "argument" in cwt.cwt_status_string(1)
+    assert cwt.cwt_status_string(99) == "unknown status"
+
+
+def test_paper_grid_matches_sec_3_1(cwt):
+    # w~ = w~_min 2^{i + j/N_subs}, w~_min = c_w pi / N, N_levs = Nint(log2 N)
+    N, n_subs = 1000, 3
+    g = cwt.cwt_scales_paper_grid(N, "gdw", 6.0, n_subs)
+    n_levs = round(math.log2(N))
+    assert len(g) == n_levs * n_subs
+    cw = 2 / math.sqrt(5)
+    assert g[0] == pytest.approx(cw * math.pi / N, rel=1e-15)
+    assert np.allclose(g[1:] / g[:-1], 2 ** (1 / n_subs), rtol=1e-13)
+    gm = cwt.cwt_scales_paper_grid(N, "morlet", 6.0, n_subs)
+    assert gm[0] == pytest.approx(2 / (6 + math.sqrt(38)) * math.pi / N, rel=1e-15)
+
+
+@pytest.mark.parametrize("kwargs,status", [
+    (dict(N=1, scales=[2.0]), 1),
+    (dict(N=64, scales=[]), 1),
+    (dict(N=64, scales=[2.0, -1.0]), 1),
+    (dict(N=64, scales=[2.0, float("nan")]), 1),
+    (dict(N=64, scales=[2.0, float("inf")]), 1),
+    (dict(N=64, scales=[2.0], dx=0.0), 1),
+    (dict(N=64, scales=[2.0], eps_trunc=-1.0), 1),
+    (dict(N=64, scales=[2.0], wavelet="morlet", omega0=0.0), 1),
+    (dict(N=100, scales=[2.0], boundary="periodic"), 2),         # periodic needs 2^k here
+    (dict(N=64, scales=[2.0], boundary="zero", fft_len=32), 1),   # shorter than N
+    (dict(N=64, scales=[2.0], boundary="zero", fft_len=96), 2),   # not 2^k
+    (dict(N=64, scales=[2.0], boundary="periodic", fft_len=128), 1),
+    (dict(N=1 << 26, scales=[2.0], boundary="zero"), 2),          # M > 2^25
+])
+def test_plan_argument_checks(cwt, kwargs, status):
+    kw = dict(kwargs)
+    N, scales = kw.pop("N"), kw.pop("scales")
+    with pytest.raises(cwt.CwtError) as e:
+        cwt.cwt_plan_create(N, scales, **kw)
+    assert e.value.status == status
+
+
+def test_null_plan_pointers_rejected(cwt):
+    lib = cwt.load_library()
+    assert lib.cwt_exec(None, None, None, None) == 1
+    assert lib.cwt_wavelet_power(None, None, None, None) == 1
+    assert lib.cwt_plan_create(None, 64, None, 1, 0, 0) == 1
+    assert lib.cwt_plan_destroy(None) == 0
+    n = ctypes.c_int32()
+    assert lib.cwt_scales_paper_grid(1, 0, 6.0, 2, None, ctypes.byref(n)) == 1

@@ -1,0 +1,208 @@
+"""Parity of the CUDA FFTCWT (through the C ABI) with the FP64 CPU oracle.
+
+Gate: relative L2 error <= 1e-5 over the whole W array (FP32 path), per
+configuration.  Small cases are compared element by element with the oracle's
+full arrays; the large workloads in the launch configuration the benchmark
+times are compared on the full array where the oracle finishes in seconds and
+on sampled outputs (each computed on its own by the oracle) otherwise.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    import paper_2302_03909_gb300 as cwt
+    cwt.load_library()
+    oracle.build()
+    return torch, cwt, oracle
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(env, f, scales, wavelet, boundary, dtype="f32", power=True, **kw):
+    torch, cwt, _ = env
+    plan = cwt.cwt_plan_create(len(f), scales, wavelet, boundary, input_dtype=dtype, **kw)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    sig = torch.tensor(f, dtype=tdt, device="cuda")
+    if power:
+        W, spec = cwt.cwt_exec_with_power(plan, sig)
+    else:
+        W, spec = cwt.cwt_exec(plan, sig), None
+    torch.cuda.synchronize()
+    out = W.cpu().numpy().astype(np.complex128)
+    sp = spec.cpu().numpy() if spec is not None else None
+    M = plan.M
+    plan.close()
+    return out, sp, M
+
+
+def f32(f):
+    # the device computes on the FP32-rounded signal; the oracle gets the same values
+    return np.asarray(f, dtype=np.float32).astype(np.float64)
+
+
+# ------------------------------------------------- the smallest paper-shaped case
+
+def test_multitone_4096_gdw_against_direct_sum(env):
+    """One FP64 multitone signal, N = 4096, periodic, GDW, 32 log-spaced scales
+    2..1024: W against the direct sum of Eq. 4 over the whole array."""
+    _, _, orc = env
+    name = "multitone_n4096_gdw_s32"
+    f = synth.workload_signal(name)
+    sc = synth.workload_scales(name)
+    W, spec, M = run_gpu(env, f, sc, "gdw", "periodic", dtype="f64")
+    direct = orc.cwt_direct(f32(f), sc, "gdw", "periodic")
+    dft = orc.cwt_fft(f32(f), sc, "gdw")
+    assert rel_l2(dft, direct) < 1e-12          # the definition and the FFTCWT agree here
+    assert rel_l2(W, direct) <= TOL
+    assert np.max(np.abs(W.imag)) == 0.0
+    P = orc.wavelet_power(dft)
+    assert np.max(np.abs(spec - P) / P) < 1e-5
+
+
+# ------------------------------------------------- small sizes, every code path
+
+CASES = [
+    # N, boundary, wavelet, s_min, s_max, n_scales, extra plan options
+    (2, "periodic", "gdw", 0.5, 4.0, 3, {}),
+    (8, "periodic", "morlet", 0.3, 64.0, 5, {}),
+    (64, "zero", "gdw", 1.0, 100.0, 7, {}),
+    (1000, "zero", "morlet", 2.0, 900.0, 9, {}),
+    (1000, "zero", "gdw", 2.0, 300.0, 1, {}),
+    (4096, "periodic", "morlet", 4.0, 2048.0, 16, {}),
+    (4097, "zero", "gdw", 1.5, 4000.0, 11, {}),
+    (1 << 14, "periodic", "gdw", 2.0, 4096.0, 13, {}),
+    (1 << 14, "zero", "morlet", 3.0, 4096.0, 12, {}),
+    (1 << 16, "periodic", "morlet", 4.0, 1 << 14, 10, {}),
+    ((1 << 16) + 5, "zero", "gdw", 2.0, 1 << 14, 9, {}),
+    (1 << 17, "periodic", "gdw", 2.0, 1 << 15, 7, {"eps_trunc": 0.0}),
+    (3000, "zero", "morlet", 5.0, 600.0, 6, {"fft_len": 1 << 14}),
+    (1 << 12, "periodic", "morlet", 4.0, 1000.0, 6, {"omega0": 4.0, "dx": 0.25}),
+]
+
+
+@pytest.mark.parametrize("N,boundary,wavelet,smin,smax,S,kw", CASES)
+def test_small_parity(env, N, boundary, wavelet, smin, smax, S, kw):
+    _, _, orc = env
+    f = synth.lognormal_field(N, seed=N + S)
+    sc = synth.log_scales(smin, smax, S)
+    W, spec, M = run_gpu(env, f, sc, wavelet, boundary, **kw)
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=M, omega0=kw.get("omega0", 6.0), dx=kw.get("dx", 1.0))
+    assert rel_l2(W, ref) <= TOL
+    # each row on its own, so a wrong scale cannot hide behind a large one
+    for s in range(S):
+        nr = np.linalg.norm(ref[s])
+        if nr > 1e-6 * np.linalg.norm(ref):
+            assert np.linalg.norm(W[s] - ref[s]) / nr <= 10 * TOL, s
+    P = orc.wavelet_power(ref)
+    mask = P > 1e-12 * P.max()
+    assert np.max(np.abs(spec[mask] - P[mask]) / P[mask]) < 1e-4
+
+
+def test_w_tilde_units_and_paper_grid(env):
+    torch, cwt, orc = env
+    N = 2048
+    f = synth.multitone(N, seed=3)
+    wt = cwt.cwt_scales_paper_grid(N, "morlet", 6.0, 3)
+    W, _, M = run_gpu(env, f, wt, "morlet", "periodic", scale_unit="w_tilde")
+    ref = orc.cwt_fft(f32(f), wt, "morlet", w_tilde=True)
+    assert rel_l2(W, ref) <= TOL
+
+
+def test_standalone_power_and_host_path(env):
+    torch, cwt, orc = env
+    N = 1 << 15
+    f = synth.lognormal_field(N, seed=5)
+    sc = synth.log_scales(4.0, 8000.0, 10)
+    plan = cwt.cwt_plan_create(N, sc, "morlet", "zero")
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    W, spec = cwt.cwt_exec_with_power(plan, sig)
+    spec2 = cwt.cwt_wavelet_power(plan, W)
+    torch.cuda.synchronize()
+    ref = orc.wavelet_power(W.cpu().numpy().astype(np.complex128))
+    assert np.max(np.abs(spec2.cpu().numpy() - ref) / ref) < 1e-6
+    assert np.max(np.abs(spec.cpu().numpy() - ref) / ref) < 1e-6
+    Wh = np.empty((10, N), dtype=np.complex64)
+    sh = np.empty(10, dtype=np.float64)
+    cwt.cwt_exec_host(plan, f.astype(np.float32), Wh, sh)
+    assert np.array_equal(Wh, W.cpu().numpy())
+    assert np.array_equal(sh, spec.cpu().numpy())
+    plan.close()
+
+
+def test_repeatable_bitwise(env):
+    torch, cwt, _ = env
+    N = 1 << 16
+    f = synth.lognormal_field(N, seed=9)
+    sc = synth.log_scales(2.0, 1 << 14, 12)
+    plan = cwt.cwt_plan_create(N, sc, "gdw", "zero")
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    W1, s1 = cwt.cwt_exec_with_power(plan, sig)
+    W2, s2 = cwt.cwt_exec_with_power(plan, sig)
+    torch.cuda.synchronize()
+    assert torch.equal(W1, W2) and torch.equal(s1, s2)
+    plan.close()
+
+
+def test_exec_argument_checks(env):
+    torch, cwt, _ = env
+    plan = cwt.cwt_plan_create(64, [2.0, 4.0], "morlet", "periodic")
+    lib = cwt.load_library()
+    sig = torch.zeros(64, device="cuda")
+    W = plan.empty_output()
+    import ctypes
+    bad = ctypes.c_void_p(W.data_ptr() + 4)          # complex64 output must be 8-byte aligned
+    assert lib.cwt_exec(plan._h, ctypes.c_void_p(sig.data_ptr()), bad, None) == 1
+    assert lib.cwt_exec(plan._h, None, ctypes.c_void_p(W.data_ptr()), None) == 1
+    plan.close()
+
+
+# ------------------------------------------------- full-size workloads
+
+def _full_case(env, name, boundary, points=256, full_oracle=False):
+    torch, cwt, orc = env
+    f = synth.workload_signal(name)
+    sc = synth.workload_scales(name)
+    wav = synth.WORKLOADS[name]["wavelet"]
+    W, spec, M = run_gpu(env, f, sc, wav, boundary)
+    ps, pn = synth.sample_points(len(sc), len(f), points, seed=len(f) + len(sc))
+    ref_pts = orc.cwt_fft_points(f32(f), sc, wav, ps, pn, M=M)
+    got_pts = W[ps, pn]
+    # sampled outputs, normalised by the row norms (the whole-array norm is not
+    # available without the full oracle)
+    assert rel_l2(got_pts, ref_pts) <= TOL
+    if full_oracle:
+        ref = orc.cwt_fft(f32(f), sc, wav, M=M)
+        assert rel_l2(W, ref) <= TOL
+        P = orc.wavelet_power(ref)
+        assert np.max(np.abs(spec - P) / P) < 1e-4
+    if boundary == "periodic":
+        # psi_hat(0) = 0: every periodic row has zero mean
+        mean = np.abs(W.mean(axis=1))
+        assert np.all(mean <= 1e-5 * np.sqrt(spec) + 1e-12)
+    return W
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "zero"])
+def test_lognormal_1m_morlet_64(env, boundary):
+    """N = 2^20 lognormal field, Morlet omega0 = 6, 64 scales: full-array parity."""
+    _full_case(env, "lognormal_n1m_morlet_s64", boundary, full_oracle=True)
+
+
+@pytest.mark.parametrize("name", ["lognormal_n4m_gdw_s128", "lognormal_n4m_morlet_s128"])
+@pytest.mark.parametrize("boundary", ["periodic", "zero"])
+def test_lognormal_4m_128_sampled(env, name, boundary):
+    """N = 2^22, 128 scales: sampled outputs against the oracle, one by one."""
+    _full_case(env, name, boundary, points=192)
