@@ -163,6 +163,40 @@ cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable);
 cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t kernel_class, double* total_ms, int64_t* launches,
                                double* algorithmic_bytes);
 
+/* Power spectrum without any allocation.
+ *
+ * Same result and layout as cwt_wavelet_power (one row of W per scale; f32
+ * rows if is_complex == 0, interleaved complex64 rows otherwise;
+ * spectrum_dev[s] = (1/N) sum_n |W(s,n)|^2 in float64), but it needs no plan
+ * and calls no cudaMalloc, cudaFree or allocating library routine.  It is for
+ * callers that cannot allocate device memory at the point of the call: a
+ * process whose device memory is all reserved by another allocator (a
+ * framework's caching allocator or a serving worker that has budgeted every
+ * byte), or a latency-critical loop that must not pay for the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this
+ * is a deployment convenience.
+ *
+ * Scratch: the partial sums live in one fixed device array inside the library,
+ * CWT_NOALLOC_MAX_PARTIALS doubles (512 KiB), held on every device that loads
+ * the library until the process exits.  Each row is split into chunks of
+ * CWT_NOALLOC_CHUNK samples, so a call needs n_scales * ceil(N /
+ * CWT_NOALLOC_CHUNK) partial sums; larger requests are rejected with
+ * CWT_ERR_UNSUPPORTED before any launch (e.g. N = 2^22 allows up to 512 scales,
+ * N = 2^24 up to 128).  Every call overwrites the partial sums it reads, so no
+ * clearing is needed, but all calls share the one array: calls whose kernels
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture on the device.  W_dev and spectrum_dev are device pointers of
+ * the current device, 4 B (f32) / 8 B (complex64, spectrum) aligned; N >= 1,
+ * n_scales >= 1, otherwise CWT_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+#define CWT_NOALLOC_MAX_PARTIALS 65536
+#define CWT_NOALLOC_CHUNK 32768
+cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, int32_t n_scales, int32_t is_complex,
+                                     double* spectrum_dev, void* stream);
+
 /* Static description of a status code. */
 const char* cwt_status_string(cwt_status status);
 

@@ -22,7 +22,7 @@ from . import build as _build
 __all__ = [
     "CwtError", "Plan", "cwt_plan_create", "cwt_plan_destroy", "cwt_plan_info", "cwt_exec",
     "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host", "cwt_scales_paper_grid",
-    "cwt_status_string", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
+    "cwt_status_string", "cwt_wavelet_power_noalloc", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
     "ABI_FUNCTIONS", "KERNEL_CLASSES",
 ]
 
@@ -36,8 +36,10 @@ ABI_FUNCTIONS = [
     "cwt_plan_opts_default", "cwt_plan_create", "cwt_plan_create_ex", "cwt_plan_destroy",
     "cwt_plan_info", "cwt_exec", "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host",
     "cwt_scales_paper_grid", "cwt_status_string", "cwt_plan_last_error", "cwt_plan_set_timing",
-    "cwt_plan_get_timing",
+    "cwt_plan_get_timing", "cwt_wavelet_power_noalloc",
 ]
+NOALLOC_MAX_PARTIALS = 65536
+NOALLOC_CHUNK = 32768
 KERNEL_CLASSES = {"forward": 0, "band": 1, "wide1": 2, "wide2": 3, "power": 4}
 
 
@@ -97,6 +99,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.cwt_plan_set_timing.argtypes = [vp, i32]
         lib.cwt_plan_get_timing.restype = ctypes.c_int
         lib.cwt_plan_get_timing.argtypes = [vp, i32, pd, ctypes.POINTER(i64), pd]
+        lib.cwt_wavelet_power_noalloc.restype = ctypes.c_int
+        lib.cwt_wavelet_power_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
         _lib = lib
         return lib
 
@@ -271,6 +275,26 @@ def cwt_exec_host(plan: Plan, signal, W, spectrum=None, stream=None):
     _check(load_library().cwt_exec_host(plan._h, hptr(signal), hptr(W), sp, _stream_ptr(stream)),
            plan)
     return W, spectrum
+
+
+def cwt_wavelet_power_noalloc(W, spectrum, stream=None):
+    """Power spectrum of W (rows = scales) with no plan and no device allocation:
+    the library keeps its partial sums in a fixed device array, so the caller
+    must pre-allocate `spectrum` (n_scales float64) and serialise calls that
+    could overlap on the GPU.  Rejects n_scales * ceil(N / 32768) > 65536."""
+    import torch
+    if W.dim() != 2 or W.dtype not in (torch.float32, torch.complex64):
+        raise ValueError("W must be a 2-D float32 or complex64 CUDA tensor")
+    S, N = W.shape
+    if spectrum.dtype != torch.float64 or spectrum.numel() != S:
+        raise ValueError("spectrum must hold n_scales float64 values")
+    st = load_library().cwt_wavelet_power_noalloc(_dev_ptr(W, "W"), N, S, int(W.dtype == torch.complex64),
+                                                  _dev_ptr(spectrum, "spectrum"), _stream_ptr(stream))
+    if st == 2:
+        need = S * -(-N // NOALLOC_CHUNK)
+        raise CwtError(st, f"{need} partial sums needed, the static scratch holds {NOALLOC_MAX_PARTIALS}")
+    _check(st)
+    return spectrum
 
 
 def cwt_plan_set_timing(plan: Plan, enable: bool = True):

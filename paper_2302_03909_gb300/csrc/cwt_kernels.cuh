@@ -398,9 +398,9 @@ __global__ void __launch_bounds__(NT) k_pass1(Params p, const Job* __restrict__ 
 // ------------------------------------------------------------ power
 
 // spectrum[s] = (sum of the row's partials in fixed order) / N
-__global__ void k_power_finalize(const double* __restrict__ partials, const int32_t* __restrict__ off,
-                                 const int32_t* __restrict__ cnt, int32_t S, int64_t N,
-                                 double* __restrict__ spectrum) {
+static __global__ void k_power_finalize(const double* __restrict__ partials, const int32_t* __restrict__ off,
+                                        const int32_t* __restrict__ cnt, int32_t S, int64_t N,
+                                        double* __restrict__ spectrum) {
     int s = blockIdx.x;
     if (s >= S) return;
     double acc = 0.0;
@@ -411,8 +411,8 @@ __global__ void k_power_finalize(const double* __restrict__ partials, const int3
 }
 
 // spectrum[s] = (sum_c partials[s * chunks + c] in fixed order) / N
-__global__ void k_power_finalize_uniform(const double* __restrict__ partials, int32_t chunks, int32_t S, int64_t N,
-                                         double* __restrict__ spectrum) {
+static __global__ void k_power_finalize_uniform(const double* __restrict__ partials, int32_t chunks, int32_t S,
+                                                int64_t N, double* __restrict__ spectrum) {
     int s = blockIdx.x;
     if (s >= S) return;
     double acc = 0.0;
