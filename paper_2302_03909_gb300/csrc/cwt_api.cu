@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cwt.h"
@@ -18,72 +19,79 @@ using namespace cwtk;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
-constexpr int kMaxLogM = 25;          // M <= 2^25 (zero boundary of N = 2^24)
-constexpr int kSingleMaxLogB = 10;    // single-pass DFT length when M > kLmax
-constexpr int kMaxDepth = 4;          // direct depth of the single-pass kernel
+constexpr int kMaxLogM = 25;           // M <= 2^25 (zero boundary of N = 2^24)
+constexpr int kBandMaxLog = 12;        // band kernels up to L = 4096 when M > kLmax
+constexpr int kWideLog = 10;           // pass-2 DFT length of wide scales (M <= 2^23)
+constexpr size_t kWideBatchBytes = size_t(64) << 20;   // intermediate per wide launch (L2-sized)
 
 // ----------------------------------------------------------- launch shapes
 
-constexpr int final_T(int logb) {
-    int t = kTileElems >> logb;
-    return t < 1 ? 1 : (t > 64 ? 64 : t);
+// threads per CTA are T * max_bfly(LOGL); aim at 256 threads (128 for one-stage DFTs)
+constexpr int kThreadsTarget = 256;
+// (three-stage DFTs keep 4 columns for 32-byte output runs, 1 at L = 8192)
+constexpr int band_T(int logl) {
+    return n_stages(logl) == 1 ? 128
+         : n_stages(logl) == 3 ? (logl >= 13 ? 1 : 4)
+         : (kThreadsTarget / max_bfly(logl) < 1 ? 1 : kThreadsTarget / max_bfly(logl));
 }
-constexpr int final_NT(int logb) {
-    int e = (1 << logb) * final_T(logb) / 8;
-    return e < 32 ? 32 : (e > 256 ? 256 : e);
-}
-constexpr int final_pad(int logb) {
-    return (final_T(logb) < 16 && final_T(logb) > 1) ? 1 : 0;
-}
-constexpr int p1_T(int loga) {
-    int t = kTileElems >> loga;
-    return t < 1 ? 1 : (t > 16 ? 16 : t);
-}
-constexpr int p1_NT(int loga) {
-    int e = (1 << loga) * p1_T(loga) / 8;
-    return e < 32 ? 32 : (e > 256 ? 256 : e);
-}
+constexpr int wide1_T(int loga) { return band_T(loga); }
+// pruned pass 1: at most 32 columns d1 per tile (A1 = A / L1 can be small)
+constexpr int wide1p_T(int logl) { return band_T(logl) > 32 ? 32 : band_T(logl); }
 
-using FinalFn = void (*)(Params, const Job*, const int32_t*);
-using Pass1Fn = void (*)(Params, const Job*);
+using KernFn = void (*)(Params);
+struct Entry { KernFn fn; int T, NT, logl; };
 
-struct FinalEntry { FinalFn fn; int T, NT; };
-struct Pass1Entry { Pass1Fn fn; int T1, NT; };
+template <int LOGL, int T>
+Entry band_entry() { return {k_band<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry wide2_entry() { return {k_wide2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 
-template <int LOGB, int SRC, int SINK>
-FinalEntry final_entry() {
-    return {k_final<LOGB, final_T(LOGB), final_NT(LOGB), SRC, SINK>, final_T(LOGB), final_NT(LOGB)};
-}
-template <int LOGA, int MODE>
-Pass1Entry pass1_entry() {
-    return {k_pass1<LOGA, p1_T(LOGA), p1_NT(LOGA), MODE>, p1_T(LOGA), p1_NT(LOGA)};
-}
+using KernFnP = void (*)(Params, int, int);
+struct EntryP { KernFnP fn; int T, NT, logl; };
+template <int LOGL, int T>
+EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 
-template <int SRC, int SINK, int... L>
-void fill_final(FinalEntry* tab, std::integer_sequence<int, L...>) {
-    ((tab[L + 1] = final_entry<L + 1, SRC, SINK>()), ...);
-}
-template <int MODE, int... L>
-void fill_pass1(Pass1Entry* tab, std::integer_sequence<int, L...>) {
-    ((tab[L + 1] = pass1_entry<L + 1, MODE>()), ...);
+template <int... L>
+void fill_tables(Entry* band, Entry* wide1, Entry* fwd1, Entry* fwd_small, EntryP* wide1p,
+                 std::integer_sequence<int, L...>) {
+    ((band[L + 1] = band_entry<L + 1, band_T(L + 1)>()), ...);
+    ((wide1p[L + 1] = wide1p_entry<L + 1, wide1p_T(L + 1)>()), ...);
+    ((wide1[L + 1] = wide1_entry<L + 1, wide1_T(L + 1)>()), ...);
+    ((fwd1[L + 1] = fwd1_entry<L + 1, wide1_T(L + 1)>()), ...);
+    ((fwd_small[L + 1] = fwd2_entry<L + 1, 1>()), ...);
 }
 
 struct Tables {
-    FinalEntry band_w[kLmaxLog + 1];     // single pass, band source, W sink
-    FinalEntry y_w[kLmaxLog + 1];        // pass 2 of the inverse
-    FinalEntry y_fwd[kLmaxLog + 1];      // pass 2 of the forward
-    FinalEntry sig_fwd[kLmaxLog + 1];    // one-tile forward
-    Pass1Entry p1_band[kLmaxLog + 1];
-    Pass1Entry p1_sig[kLmaxLog + 1];
+    Entry band[kLmaxLog + 1];
+    Entry wide1[kLmaxLog + 1];
+    Entry fwd1[kLmaxLog + 1];
+    Entry fwd_small[kLmaxLog + 1];
+    Entry wide2[kLmaxLog + 1];
+    Entry fwd2[kLmaxLog + 1];
+    EntryP wide1p[kLmaxLog + 1];
     Tables() {
         std::memset((void*)this, 0, sizeof(*this));
-        auto seq = std::make_integer_sequence<int, kLmaxLog>{};
-        fill_final<SRC_BAND, SINK_W>(band_w, seq);
-        fill_final<SRC_Y, SINK_W>(y_w, seq);
-        fill_final<SRC_Y, SINK_FWD>(y_fwd, seq);
-        fill_final<SRC_SIGNAL, SINK_FWD>(sig_fwd, seq);
-        fill_pass1<P1_BAND>(p1_band, seq);
-        fill_pass1<P1_SIGNAL>(p1_sig, seq);
+        fill_tables(band, wide1, fwd1, fwd_small, wide1p, std::make_integer_sequence<int, kLmaxLog - 2>{});
+        wide1[12] = wide1_entry<12, wide1_T(12)>();
+        wide1[13] = wide1_entry<13, wide1_T(13)>();
+        fwd1[12] = fwd1_entry<12, wide1_T(12)>();
+        fwd1[13] = fwd1_entry<13, wide1_T(13)>();
+        band[12] = band_entry<12, band_T(12)>();
+        band[13] = band_entry<13, band_T(13)>();
+        fwd_small[12] = fwd2_entry<12, 1>();
+        fwd_small[13] = fwd2_entry<13, 1>();
+        wide2[10] = wide2_entry<10, band_T(10)>();
+        wide2[11] = wide2_entry<11, band_T(11)>();
+        wide2[12] = wide2_entry<12, band_T(12)>();
+        fwd2[10] = fwd2_entry<10, band_T(10)>();
+        fwd2[11] = fwd2_entry<11, band_T(11)>();
+        fwd2[12] = fwd2_entry<12, band_T(12)>();
     }
 };
 
@@ -144,13 +152,15 @@ struct cwt_plan {
     std::vector<double> w_tilde;
 
     std::vector<Job> jobs;
-    struct Group { int logb; int T_eff; int ntiles; int kmax; size_t tj_off; std::vector<int> job_ids; };
-    std::vector<Group> groups;            // single-pass jobs by DFT length
-    std::vector<int> two_pass;            // jobs using pass 1 + pass 2
-    int tp_loga = 0, tp_logb = 0, tp_T_eff = 0, tp_ntiles2 = 0;
-    int fwd_small = 0, fwd_loga = 0, fwd_logb = 0, fwd_T_eff = 0;
+    struct BandGroup { int logl; int ntiles; size_t tj_off; double bytes; };
+    std::vector<BandGroup> groups;        // single-pass jobs by DFT length
+    struct WideBatch { int job0; int count; int logl1; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
+    std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
+    int wide_logl = 0, wide_loga = 0, wide_G = 0;
+    int fwd_small = 0;
     int64_t n_partials = 0;
     std::vector<int32_t> part_off, part_cnt;
+    int64_t n_band_jobs = 0;
 
     // device memory
     Job* d_jobs = nullptr;
@@ -162,7 +172,7 @@ struct cwt_plan {
     double* d_partials = nullptr;
     float2* d_tw_lo = nullptr;
     float2* d_tw_hi = nullptr;
-    float2* d_tw_L = nullptr;
+    float2* d_tw_tab = nullptr;
     size_t ws_bytes = 0;
     // cwt_exec_host buffers
     void* h_sig = nullptr;
@@ -180,8 +190,6 @@ struct cwt_plan {
     double t_ms[CWT_KCLASS_COUNT] = {};
     int64_t t_launches[CWT_KCLASS_COUNT] = {};
     double t_bytes[CWT_KCLASS_COUNT] = {};
-    // algorithmic bytes of each launch group
-    std::vector<double> group_bytes;
     double fwd_in_bytes = 0, fwd_out_bytes = 0;
 
     std::string err;
@@ -235,15 +243,18 @@ void free_plan(cwt_plan* p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     p->ev_pool.clear();
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Y,
-                    p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_L, p->h_sig, p->h_W,
+                    p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
 }
 
-double out_row_bytes(const cwt_plan* p);
-double job_rows(const Job& J);
+double out_row_bytes(const cwt_plan* p) {
+    return (double)p->N * (p->wavelet == CWT_WAVELET_MORLET ? 8.0 : 4.0);
+}
+
+double job_rows(const Job& J) { return (J.g[0].row >= 0) + (J.g[1].row >= 0); }
 
 ScaleGen make_gen(const cwt_plan* p, double wt, int row) {
     ScaleGen g{};
@@ -273,6 +284,8 @@ void scale_band(const cwt_plan* p, double wt, double u_lo, double u_hi, int64_t*
     *khi = hi;
 }
 
+size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_stride(T) * sizeof(float2); }
+
 cwt_status build_plan(cwt_plan* p) {
     const Tables& tb = tables();
     const int64_t M = p->M;
@@ -282,6 +295,7 @@ cwt_status build_plan(cwt_plan* p) {
 
     // jobs: GDW pairs (2i, 2i+1); Morlet one scale each
     const int per = (p->wavelet == CWT_WAVELET_GDW) ? 2 : 1;
+    std::vector<Job> all;
     for (int s0 = 0; s0 < p->S; s0 += per) {
         Job J{};
         int64_t klo = 0, khi = -1;
@@ -301,35 +315,24 @@ cwt_status build_plan(cwt_plan* p) {
         }
         J.k_lo = (int32_t)klo;
         J.K = (int32_t)(khi - klo + 1);
-        p->jobs.push_back(J);
+        all.push_back(J);
     }
 
-    // transform shapes
+    // shapes: band kernels take K <= L (L <= 1024, or <= M when M <= kLmax); wider bands
+    // take the two-pass path with pass-2 length 2^wide_logl
     const bool small = M <= kLmax;
-    p->tp_logb = std::max(kSingleMaxLogB, p->logM - kLmaxLog);
-    p->tp_loga = p->logM - p->tp_logb;
-    std::vector<std::vector<int>> by_logb(kLmaxLog + 1);
-    for (int j = 0; j < (int)p->jobs.size(); j++) {
-        Job& J = p->jobs[j];
+    p->wide_logl = std::max(kWideLog, p->logM - kLmaxLog);
+    p->wide_loga = p->logM - p->wide_logl;
+    std::vector<std::vector<Job>> by_logl(kLmaxLog + 1);
+    std::vector<Job> wide;
+    for (const Job& J : all) {
         int lk = std::max(1, ilog2(J.K));
-        if (small) {
-            int lb = std::min(lk, p->logM);
-            J.r = (int32_t)((J.K + (1 << lb) - 1) >> lb);
-            by_logb[lb].push_back(j);
-        } else if (lk <= kSingleMaxLogB) {
-            J.r = 1;
-            by_logb[lk].push_back(j);
-        } else if (J.K <= kMaxDepth << kSingleMaxLogB) {
-            J.r = (int32_t)((J.K + (1 << kSingleMaxLogB) - 1) >> kSingleMaxLogB);
-            by_logb[kSingleMaxLogB].push_back(j);
-        } else {
-            J.r = 0;
-            J.tile0 = 0;
-            p->two_pass.push_back(j);
-        }
+        if (small) by_logl[std::min(lk, p->logM)].push_back(J);
+        else if (lk <= kBandMaxLog) by_logl[lk].push_back(J);
+        else wide.push_back(J);
     }
 
-    // single-pass groups and their tile -> job maps; power partial layout
+    // band groups (jobs reordered: band groups first, then wide batches)
     std::vector<int32_t> tile_job;
     p->part_off.assign(p->S, 0);
     p->part_cnt.assign(p->S, 0);
@@ -343,57 +346,61 @@ cwt_status build_plan(cwt_plan* p) {
             nparts += ntiles;
         }
     };
-    for (int lb = 1; lb <= kLmaxLog; lb++) {
-        if (by_logb[lb].empty()) continue;
-        cwt_plan::Group g;
-        g.logb = lb;
-        int64_t A = M >> lb;
-        g.T_eff = (int)std::min<int64_t>(tb.band_w[lb].T, A);
-        int per_job = (int)(A / g.T_eff);
+    for (int ll = 1; ll <= kLmaxLog; ll++) {
+        if (by_logl[ll].empty()) continue;
+        cwt_plan::BandGroup g;
+        g.logl = ll;
+        const int64_t A = M >> ll;
+        const int T = tb.band[ll].T;
+        const int per_job = (int)((A + T - 1) / T);
         g.ntiles = 0;
-        g.kmax = 0;
         g.tj_off = tile_job.size();
-        for (int j : by_logb[lb]) {
-            Job& J = p->jobs[j];
+        g.bytes = 0;
+        for (Job J : by_logl[ll]) {
             J.tile0 = g.ntiles;
-            for (int t = 0; t < per_job; t++) tile_job.push_back(j);
+            int idx = (int)p->jobs.size();
+            for (int t = 0; t < per_job; t++) tile_job.push_back(idx);
             g.ntiles += per_job;
-            g.kmax = std::max(g.kmax, (int)J.K);
             assign_parts(J, per_job);
-            g.job_ids.push_back(j);
+            g.bytes += job_rows(J) * out_row_bytes(p) + 8.0 * J.K;
+            p->jobs.push_back(J);
         }
         p->groups.push_back(g);
     }
-    if (!p->two_pass.empty()) {
-        int64_t A = M >> p->tp_logb;
-        p->tp_T_eff = (int)std::min<int64_t>(tb.y_w[p->tp_logb].T, A);
-        p->tp_ntiles2 = (int)(A / p->tp_T_eff);
-        for (int j : p->two_pass) assign_parts(p->jobs[j], p->tp_ntiles2);
+    p->n_band_jobs = (int64_t)p->jobs.size();
+    if (!wide.empty()) {
+        const int64_t A = M >> p->wide_logl;
+        const int T2 = tb.wide2[p->wide_logl].T;
+        const int ntiles2 = (int)((A + T2 - 1) / T2);
+        p->wide_G = (int)std::max<int64_t>(1, (int64_t)(kWideBatchBytes / ((size_t)M * sizeof(float2))));
+        const int L = 1 << p->wide_logl;
+        for (size_t i = 0; i < wide.size(); i++) {
+            Job J = wide[i];
+            // pass 1 of column b has at most ceil(K / L) band bins: a pruned band tile of
+            // L1 = 2^ceil(log2) points unless that is most of the A-point DFT
+            int l1 = std::max(1, ilog2(((int64_t)J.K + L - 1) / L));
+            // prune only when the A1 = A / L1 columns d1 fill at least one tile
+            if (l1 > kLmaxLog - 2 || l1 > p->wide_loga || (int64_t(1) << (p->wide_loga - l1)) < tb.wide1p[l1].T)
+                l1 = -1;
+            if (p->wide.empty() || p->wide.back().count >= p->wide_G || p->wide.back().logl1 != l1)
+                p->wide.push_back({(int)p->jobs.size(), 0, l1, 0.0, 0.0});
+            J.tile0 = 0;
+            assign_parts(J, ntiles2);
+            auto& wb = p->wide.back();
+            wb.count++;
+            wb.band_bytes += 8.0 * J.K;
+            wb.out_bytes += job_rows(J) * out_row_bytes(p);
+            p->jobs.push_back(J);
+        }
     }
     p->n_partials = nparts;
-    for (const auto& g : p->groups) {
-        double b = 0;
-        for (int j : g.job_ids) b += job_rows(p->jobs[j]) * out_row_bytes(p) + 8.0 * p->jobs[j].K;
-        p->group_bytes.push_back(b);
-    }
+    p->fwd_small = small;
     p->fwd_in_bytes = (double)p->N * (p->opts.input_dtype == CWT_INPUT_F64 ? 8.0 : 4.0);
     p->fwd_out_bytes = 8.0 * (double)(M / 2 + 1);
 
-    // forward transform shape
-    if (small) {
-        p->fwd_small = 1;
-        p->fwd_logb = p->logM;
-        p->fwd_T_eff = 1;
-    } else {
-        p->fwd_small = 0;
-        p->fwd_logb = p->tp_logb;
-        p->fwd_loga = p->tp_loga;
-        p->fwd_T_eff = (int)std::min<int64_t>(tb.y_fwd[p->fwd_logb].T, M >> p->fwd_logb);
-    }
-
     // twiddle tables (FP64 generated, FP32 stored)
     p->h = (p->logM + 1) / 2;
-    std::vector<float2> lo(size_t(1) << p->h), hi(size_t(1) << (p->logM - p->h)), tl(kLmax);
+    std::vector<float2> lo(size_t(1) << p->h), hi(size_t(1) << (p->logM - p->h)), tt(2 * kLmax);
     for (size_t j = 0; j < lo.size(); j++) {
         double a = -2.0 * kPi * (double)j / (double)M;
         lo[j] = make_float2((float)std::cos(a), (float)std::sin(a));
@@ -402,10 +409,12 @@ cwt_status build_plan(cwt_plan* p) {
         double a = -2.0 * kPi * (double)(j << p->h) / (double)M;
         hi[j] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
-    for (size_t j = 0; j < tl.size(); j++) {
-        double a = -2.0 * kPi * (double)j / (double)kLmax;
-        tl[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    tt[0] = tt[1] = make_float2(1.f, 0.f);
+    for (int L = 2; L <= kLmax; L *= 2)
+        for (int i = 0; i < L; i++) {
+            double a = -2.0 * kPi * (double)i / (double)L;
+            tt[L + i] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
 
     cwt_status st;
     if ((st = upload(p, &p->d_jobs, p->jobs)) != CWT_OK) return st;
@@ -414,10 +423,12 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = upload(p, &p->d_part_cnt, p->part_cnt)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tw_lo, lo)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
-    if ((st = upload(p, &p->d_tw_L, tl)) != CWT_OK) return st;
+    if ((st = upload(p, &p->d_tw_tab, tt)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
-    if (!p->fwd_small || !p->two_pass.empty())
-        if ((st = dev_alloc(p, &p->d_Y, (size_t)M)) != CWT_OK) return st;
+    size_t ycount = 0;
+    if (!small) ycount = (size_t)M;
+    if (!p->wide.empty()) ycount = std::max(ycount, (size_t)M * (size_t)std::min<int>(p->wide_G, (int)wide.size()));
+    if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
     return CWT_OK;
 }
@@ -430,10 +441,11 @@ Params base_params(const cwt_plan* p) {
     P.partials = p->d_partials;
     P.tw_lo = p->d_tw_lo;
     P.tw_hi = p->d_tw_hi;
-    P.tw_L = p->d_tw_L;
+    P.tw_tab = p->d_tw_tab;
+    P.jobs = p->d_jobs;
+    P.tile_job = p->d_tile_job;
     P.N = p->N;
     P.M = (int32_t)p->M;
-    P.logM = p->logM;
     P.h = p->h;
     P.wavelet = p->wavelet;
     P.sig_f64 = p->opts.input_dtype == CWT_INPUT_F64;
@@ -473,42 +485,17 @@ struct LaunchTimer {
     }
 };
 
-cwt_status launch_final(cwt_plan* p, const FinalEntry& fe, int ntiles, size_t smem, const Params& P,
-                        const int32_t* tile_job, cudaStream_t s, int cls, double bytes) {
+cwt_status launch(cwt_plan* p, const Entry& e, dim3 grid, size_t smem, const Params& P, cudaStream_t s, int cls,
+                  double bytes) {
+    if (!e.fn) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
     if (smem > 48 * 1024) {
-        CWT_CUDA(p, cudaFuncSetAttribute((const void*)fe.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+        CWT_CUDA(p, cudaFuncSetAttribute((const void*)e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     LaunchTimer lt(p, cls, bytes, s);
-    fe.fn<<<ntiles, fe.NT, smem, s>>>(P, p->d_jobs, tile_job);
+    e.fn<<<grid, e.NT, smem, s>>>(P);
     CWT_CUDA(p, cudaGetLastError());
     lt.done();
     return CWT_OK;
-}
-
-cwt_status launch_pass1(cwt_plan* p, const Pass1Entry& pe, int loga, const Params& P, cudaStream_t s, int cls,
-                        double bytes) {
-    size_t smem = (size_t)pe.T1 * (size_t)((1 << loga) + 1) * sizeof(float2);
-    if (smem > 48 * 1024) {
-        CWT_CUDA(p, cudaFuncSetAttribute((const void*)pe.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-    }
-    int B = (int)(p->M >> loga);
-    LaunchTimer lt(p, cls, bytes, s);
-    pe.fn<<<B / pe.T1, pe.NT, smem, s>>>(P, p->d_jobs);
-    CWT_CUDA(p, cudaGetLastError());
-    lt.done();
-    return CWT_OK;
-}
-
-double out_row_bytes(const cwt_plan* p) {
-    return (double)p->N * (p->wavelet == CWT_WAVELET_MORLET ? 8.0 : 4.0);
-}
-
-double job_rows(const Job& J) { return (J.g[0].row >= 0) + (J.g[1].row >= 0); }
-
-size_t final_smem(int logb, int kmax) {
-    return ((size_t)(1 << logb) * (size_t)(final_T(logb) + final_pad(logb)) + (size_t)kmax) * sizeof(float2);
 }
 
 cwt_status check_device(cwt_plan* p) {
@@ -528,51 +515,64 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
 
     // 1. forward transform F(m) = sum_n f(n) e^{+2 pi i m n / M}, m <= M/2
     if (p->fwd_small) {
-        const FinalEntry& fe = tb.sig_fwd[p->fwd_logb];
+        const Entry& e = tb.fwd_small[p->logM];
         Params Q = P;
         Q.A = 1;
-        Q.T_eff = 1;
-        if ((st = launch_final(p, fe, 1, final_smem(p->fwd_logb, 0), Q, nullptr, s, CWT_KCLASS_FORWARD,
-                               p->fwd_in_bytes + p->fwd_out_bytes)) != CWT_OK)
+        if ((st = launch(p, e, dim3(1), stage_smem(p->logM, 1), Q, s, CWT_KCLASS_FORWARD,
+                         p->fwd_in_bytes + p->fwd_out_bytes)) != CWT_OK)
             return st;
     } else {
-        Params Q = P;
-        if ((st = launch_pass1(p, tb.p1_sig[p->fwd_loga], p->fwd_loga, Q, s, CWT_KCLASS_FORWARD,
-                               p->fwd_in_bytes)) != CWT_OK)
+        const Entry& e1 = tb.fwd1[p->wide_loga];
+        const int L = 1 << p->wide_logl;
+        if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga, e1.T), P, s,
+                         CWT_KCLASS_FORWARD, p->fwd_in_bytes)) != CWT_OK)
             return st;
-        const FinalEntry& fe = tb.y_fwd[p->fwd_logb];
-        Q.A = (int32_t)(p->M >> p->fwd_logb);
-        Q.T_eff = p->fwd_T_eff;
-        if ((st = launch_final(p, fe, Q.A / Q.T_eff, final_smem(p->fwd_logb, 0), Q, nullptr, s, CWT_KCLASS_FORWARD,
-                               p->fwd_out_bytes)) != CWT_OK)
+        const Entry& e2 = tb.fwd2[p->wide_logl];
+        Params Q = P;
+        Q.A = (int32_t)(p->M >> p->wide_logl);
+        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, s,
+                         CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
             return st;
     }
 
-    // 2. single-pass scales, one launch per DFT length
-    for (size_t gi = 0; gi < p->groups.size(); gi++) {
-        const auto& g = p->groups[gi];
-        const FinalEntry& fe = tb.band_w[g.logb];
+    // 2. band scales, one launch per DFT length
+    for (const auto& g : p->groups) {
+        const Entry& e = tb.band[g.logl];
         Params Q = P;
-        Q.A = (int32_t)(p->M >> g.logb);
-        Q.T_eff = g.T_eff;
-        if ((st = launch_final(p, fe, g.ntiles, final_smem(g.logb, g.kmax), Q, p->d_tile_job + g.tj_off, s,
-                               CWT_KCLASS_BAND, p->group_bytes[gi])) != CWT_OK)
-            return st;
+        Q.A = (int32_t)(p->M >> g.logl);
+        Q.tile_job = p->d_tile_job + g.tj_off;
+        size_t smem = (size_t)(1 << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
+        if ((st = launch(p, e, dim3(g.ntiles), smem, Q, s, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
     }
 
-    // 3. wide-band scales: pass 1 (A-point DFTs + twiddle) then pass 2
-    for (int j : p->two_pass) {
+    // 3. wide scales in L2-sized batches: pass 1 (A-point DFTs + twiddle) then pass 2
+    for (const auto& wb : p->wide) {
+        const Entry& e2 = tb.wide2[p->wide_logl];
+        const int L = 1 << p->wide_logl;
         Params Q = P;
-        Q.job = j;
-        const Job& J = p->jobs[j];
-        if ((st = launch_pass1(p, tb.p1_band[p->tp_loga], p->tp_loga, Q, s, CWT_KCLASS_WIDE1, 8.0 * J.K)) !=
-            CWT_OK)
-            return st;
-        const FinalEntry& fe = tb.y_w[p->tp_logb];
-        Q.A = (int32_t)(p->M >> p->tp_logb);
-        Q.T_eff = p->tp_T_eff;
-        if ((st = launch_final(p, fe, p->tp_ntiles2, final_smem(p->tp_logb, 0), Q, nullptr, s, CWT_KCLASS_WIDE2,
-                               job_rows(J) * out_row_bytes(p))) != CWT_OK)
+        Q.job0 = wb.job0;
+        Q.A = (int32_t)(p->M >> p->wide_logl);
+        if (wb.logl1 < 0) {
+            const Entry& e1 = tb.wide1[p->wide_loga];
+            if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T, wb.count), stage_smem(p->wide_loga, e1.T), Q, s,
+                             CWT_KCLASS_WIDE1, wb.band_bytes)) != CWT_OK)
+                return st;
+        } else {
+            const EntryP& e1 = tb.wide1p[wb.logl1];
+            const int A1 = Q.A >> wb.logl1;
+            const int tpb = (A1 + e1.T - 1) / e1.T;
+            size_t smem = (size_t)(1 << wb.logl1) * sizeof(float2) + stage_smem(wb.logl1, e1.T);
+            if (!e1.fn) return fail(p, CWT_ERR_INTERNAL, "missing pass-1 instantiation");
+            if (smem > 48 * 1024)
+                CWT_CUDA(p, cudaFuncSetAttribute((const void*)e1.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+            LaunchTimer lt(p, CWT_KCLASS_WIDE1, wb.band_bytes, s);
+            e1.fn<<<dim3(L * tpb, wb.count), e1.NT, smem, s>>>(Q, L, tpb);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
+        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T, wb.count), stage_smem(p->wide_logl, e2.T), Q, s,
+                         CWT_KCLASS_WIDE2, wb.out_bytes)) != CWT_OK)
             return st;
     }
 
@@ -589,6 +589,8 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
 bool aligned(const void* q, size_t a) { return ((uintptr_t)q % a) == 0; }
 
 }  // namespace
+
+// ====================================================================== ABI
 
 // ====================================================================== ABI
 

@@ -4,16 +4,22 @@
 // Z(k) = F(k) psi_hat(alpha k) amp over the signed frequency k (Eqs. 9-10).
 // psi_hat is negligible outside a band [k_lo, k_lo + K) of the scale, so each
 // inverse DFT is evaluated as a band-pruned Cooley-Tukey factorisation
-// M = A * B with output index n = d + A c (d < A, c < B):
+// M = A * L with output index n = d + A c (d < A, c < L):
 //
-//   X(d + A c) = sum_{b<B} e^{-2 pi i b c / B} Y(b, d),
-//   Y(b, d)    = sum_{k in band, k = b mod B} Z(k) e^{-2 pi i k d / M}.
+//   X(d + A c) = sum_{b<L} e^{-2 pi i b c / L} Y(b, d),
+//   Y(b, d)    = sum_{k in band, k = b mod L} Z(k) e^{-2 pi i k d / M}.
 //
-// When K <= r B the inner sum has at most r terms and is evaluated directly
-// while the shared-memory tile is filled (single-pass kernel).  Wider bands
-// use a second factorisation (pass 1: A-point DFTs over the columns b, with
-// the e^{-2 pi i b d / M} twiddle; pass 2: B-point DFTs over b).  All DFTs
-// run in shared memory as Stockham radix-2/4/8 stages.
+// Band kernel (K <= L): one CTA tile = T consecutive columns d; Y(b, d) has a
+// single term and is formed in registers while the first DFT stage is
+// loaded.  Wide kernels (K > L): pass 1 runs the A-point DFTs over the
+// columns b (x(b + L a) = Z(b + L a)) with the twiddle e^{-2 pi i b d / M}
+// into an intermediate Y[b][d]; pass 2 runs the L-point DFTs over b.
+//
+// Every CTA-level DFT is a Stockham FFT of at most three stages, each stage a
+// radix-2..32 DFT held in registers (constant twiddles folded by the
+// compiler), with stage twiddles from FP64-generated tables and one shared-
+// memory exchange between stages.  The first stage is filled straight from
+// the source and the last stage writes straight to global memory.
 //
 // Real wavelets (GDW): two scales share one complex transform,
 // Z = Z_a + i Z_b with Z_a, Z_b Hermitian, so Re X = W_a and Im X = W_b.
@@ -26,12 +32,8 @@ namespace cwtk {
 
 constexpr int kLmaxLog = 13;              // largest DFT held by one CTA
 constexpr int kLmax = 1 << kLmaxLog;
-constexpr int kTileElems = 8192;          // complex elements per CTA tile
 
 enum { WAV_GDW = 0, WAV_MORLET = 1 };
-enum { SRC_BAND = 0, SRC_Y = 1, SRC_SIGNAL = 2 };
-enum { SINK_W = 0, SINK_FWD = 1 };
-enum { P1_BAND = 0, P1_SIGNAL = 1 };
 
 // Per-scale generator of amp * psi_hat(alpha k) in FP32 from FP64-derived constants.
 struct ScaleGen {
@@ -49,25 +51,26 @@ struct Job {
     ScaleGen g[2];
     int32_t k_lo;       // signed lowest bin of the band
     int32_t K;          // band width in bins (1..M)
-    int32_t r;          // direct depth of the single-pass kernel
     int32_t tile0;      // first tile of this job within its launch
+    int32_t pad_;
 };
 
 struct Params {
     const float2* Fp;        // F(m) = sum_n f(n) e^{+2 pi i m n / M}, m in [0, M/2]
     float2* Fp_out;          // forward pass sink
-    float2* Y;               // pass-1 -> pass-2 intermediate [B][A]
+    float2* Y;               // pass-1 -> pass-2 intermediate, [job][b][d]
     const void* signal;      // N samples, f32 or f64
     void* W;                 // [S][N] f32 (GDW) or complex64 (Morlet)
     double* partials;        // power partial sums
-    const float2* tw_lo;     // e^{-2 pi i j / M}, low  h bits
-    const float2* tw_hi;     // e^{-2 pi i j / M}, high bits
-    const float2* tw_L;      // e^{-2 pi i j / kLmax}
+    const float2* tw_lo;     // e^{-2 pi i j / M}, low  h bits of j
+    const float2* tw_hi;     // e^{-2 pi i j / M}, high bits of j
+    const float2* tw_tab;    // tw_tab[L + i] = e^{-2 pi i i / L}, L = 2, 4, .., kLmax
+    const Job* jobs;
+    const int32_t* tile_job; // band launches: tile -> job
     int64_t N;
-    int32_t M, logM, h;      // M = 2^logM, two-level table split h
-    int32_t A;               // number of columns d (= M / B)
-    int32_t T_eff;           // columns per tile (<= template T)
-    int32_t job;             // job index for single-job launches
+    int32_t M, h;            // M = 2^logM, two-level table split h
+    int32_t A;               // number of columns d (= M / L)
+    int32_t job0;            // wide launches: job = job0 + blockIdx.y
     int32_t wavelet;
     int32_t sig_f64;
     int32_t do_power;
@@ -81,8 +84,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by -i
-__device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
 
 // e^{-2 pi i j / M}, j in [0, M)
 __device__ __forceinline__ float2 tw_m(const Params& p, uint32_t j) {
@@ -106,9 +107,8 @@ __device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float h
 
 // F at the signed bin k: F(-k) = conj F(k) for a real signal
 __device__ __forceinline__ float2 spec_at(const float2* __restrict__ Fp, int k) {
-    if (k >= 0) return __ldg(&Fp[k]);
-    float2 f = __ldg(&Fp[-k]);
-    return make_float2(f.x, -f.y);
+    float2 f = __ldg(&Fp[k >= 0 ? k : -k]);
+    return make_float2(f.x, k >= 0 ? f.y : -f.y);
 }
 
 // Z(k) of a job (the pointwise product of Eq. 10, scaled)
@@ -122,115 +122,183 @@ __device__ __forceinline__ float2 band_value(const Params& p, const Job& J, int 
     return make_float2(f.x * g0, f.y * g0);
 }
 
-__device__ __forceinline__ float load_signal(const Params& p, int64_t n) {
+__device__ __forceinline__ float load_signal(const Params& p, int n) {
     if (n >= p.N) return 0.f;
     return p.sig_f64 ? (float)__ldg(&((const double*)p.signal)[n]) : __ldg(&((const float*)p.signal)[n]);
 }
 
-// ------------------------------------------------------- radix-R DFTs (sign -)
+// ------------------------------------------------- register DFTs (sign -)
 
-template <int R> __device__ __forceinline__ void dft(float2* v);
-
-template <> __device__ __forceinline__ void dft<2>(float2* v) {
-    float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b); v[1] = csub(a, b);
+// cos and -sin of 2 pi q / 32
+__host__ __device__ constexpr float kc32(int q) {
+    return q == 1 ? 9.807852804e-01f : q == 2 ? 9.238795325e-01f : q == 3 ? 8.314696123e-01f
+         : q == 5 ? 5.555702330e-01f : q == 6 ? 3.826834324e-01f : q == 7 ? 1.950903220e-01f
+         : q == 9 ? -1.950903220e-01f : q == 10 ? -3.826834324e-01f : q == 11 ? -5.555702330e-01f
+         : q == 13 ? -8.314696123e-01f : q == 14 ? -9.238795325e-01f : q == 15 ? -9.807852804e-01f : 0.f;
+}
+__host__ __device__ constexpr float ks32(int q) {
+    return q == 1 ? -1.950903220e-01f : q == 2 ? -3.826834324e-01f : q == 3 ? -5.555702330e-01f
+         : q == 5 ? -8.314696123e-01f : q == 6 ? -9.238795325e-01f : q == 7 ? -9.807852804e-01f
+         : q == 9 ? -9.807852804e-01f : q == 10 ? -9.238795325e-01f : q == 11 ? -8.314696123e-01f
+         : q == 13 ? -5.555702330e-01f : q == 14 ? -3.826834324e-01f : q == 15 ? -1.950903220e-01f : 0.f;
 }
 
-template <> __device__ __forceinline__ void dft<4>(float2* v) {
-    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    float2 s13 = cadd(v[1], v[3]), d13 = cmi(csub(v[1], v[3]));
-    v[0] = cadd(s02, s13); v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13); v[3] = csub(d02, d13);
-}
-
-template <> __device__ __forceinline__ void dft<8>(float2* v) {
-    const float r = 0.70710678118654752440f;
-    float2 e[4] = {v[0], v[2], v[4], v[6]};
-    float2 o[4] = {v[1], v[3], v[5], v[7]};
-    dft<4>(e);
-    dft<4>(o);
-    // o[q] *= e^{-2 pi i q / 8}
-    o[1] = make_float2(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));
-    o[2] = cmi(o[2]);
-    o[3] = make_float2(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        v[q] = cadd(e[q], o[q]);
-        v[q + 4] = csub(e[q], o[q]);
+// x * e^{-2 pi i Q / 32}, 0 <= Q < 16
+template <int Q>
+__device__ __forceinline__ float2 mul_w32(float2 x) {
+    constexpr float r = 0.70710678118654752440f;
+    if constexpr (Q == 0) return x;
+    else if constexpr (Q == 8) return make_float2(x.y, -x.x);
+    else if constexpr (Q == 4) return make_float2(r * (x.x + x.y), r * (x.y - x.x));
+    else if constexpr (Q == 12) return make_float2(r * (x.y - x.x), -r * (x.x + x.y));
+    else {
+        constexpr float c = kc32(Q), s = ks32(Q);
+        return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
     }
 }
 
-// ------------------------------------------------------- shared-memory FFT
-
-// T columns of an L-point DFT in shared memory.  TFAST: element (l, t) at
-// l * (T + PAD) + t and threads walk t fastest; otherwise at t * (L + PAD) + l
-// and threads walk l fastest.  Columns t >= T_eff are left untouched.
-template <int LOGL, int T, int NT, bool TFAST, int PAD>
-struct SmemFFT {
-    static constexpr int L = 1 << LOGL;
-
-    __device__ static __forceinline__ int addr(int l, int t) {
-        return TFAST ? l * (T + PAD) + t : t * (L + PAD) + l;
+template <int R, int Q>
+__device__ __forceinline__ void dft_combine(float2* v, const float2* e, const float2* o) {
+    if constexpr (Q < R / 2) {
+        float2 t = mul_w32<Q * (32 / R)>(o[Q]);
+        v[Q] = cadd(e[Q], t);
+        v[Q + R / 2] = csub(e[Q], t);
+        dft_combine<R, Q + 1>(v, e, o);
     }
+}
 
-    template <int LOGR, int LOGNS>
-    __device__ static __forceinline__ void stage(float2* buf, int T_eff, const float2* __restrict__ twL) {
-        constexpr int R = 1 << LOGR;
-        constexpr int NB = (L / R) * T;                   // butterflies per stage
-        constexpr int BPT = (NB + NT - 1) / NT;           // per thread
-        constexpr int NS = 1 << LOGNS;
-        float2 v[BPT][R];
-        int jj[BPT], tt[BPT];
+// In-place R-point DFT X(q) = sum_r v(r) e^{-2 pi i r q / R}, natural order.
+template <int R>
+__device__ __forceinline__ void dft(float2* v) {
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        d13 = make_float2(d13.y, -d13.x);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else if constexpr (R > 4) {
+        float2 e[R / 2], o[R / 2];
 #pragma unroll
-        for (int q = 0; q < BPT; q++) {
-            int idx = threadIdx.x + q * NT;
-            int j, t;
-            if (TFAST) { t = idx % T; j = idx / T; }
-            else { j = idx % (L / R); t = idx / (L / R); }
-            jj[q] = j; tt[q] = t;
-            if (idx < NB && t < T_eff) {
-#pragma unroll
-                for (int r = 0; r < R; r++) v[q][r] = buf[addr(j + r * (L / R), t)];
-                if (LOGNS > 0) {
-                    int k = j & (NS - 1);
-#pragma unroll
-                    for (int r = 1; r < R; r++) {
-                        int ti = (r * k) << (kLmaxLog - LOGNS - LOGR);
-                        v[q][r] = cmul(v[q][r], __ldg(&twL[ti]));
-                    }
-                }
-                dft<R>(v[q]);
-            }
+        for (int i = 0; i < R / 2; i++) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < BPT; q++) {
-            int idx = threadIdx.x + q * NT;
-            int j = jj[q], t = tt[q];
-            if (idx < NB && t < T_eff) {
-                int k = j & (NS - 1);
-                int base = (j - k) * R + k;
-#pragma unroll
-                for (int r = 0; r < R; r++) buf[addr(base + r * NS, t)] = v[q][r];
-            }
-        }
-        __syncthreads();
+        dft<R / 2>(e);
+        dft<R / 2>(o);
+        dft_combine<R, 0>(v, e, o);
     }
+}
 
-    template <int LOGNS>
-    __device__ static __forceinline__ void stages(float2* buf, int T_eff, const float2* __restrict__ twL) {
-        if constexpr (LOGNS < LOGL) {
-            constexpr int LOGR = (LOGNS == 0 && (LOGL % 3) != 0) ? (LOGL % 3) : 3;
-            stage<LOGR, LOGNS>(buf, T_eff, twL);
-            stages<LOGNS + LOGR>(buf, T_eff, twL);
-        }
-    }
+// ------------------------------------------------------- CTA-level FFT plan
 
-    // in: natural order; out: natural order (Stockham autosort). Caller syncs before.
-    __device__ static __forceinline__ void run(float2* buf, int T_eff, const float2* __restrict__ twL) {
-        stages<0>(buf, T_eff, twL);
-    }
+// L = 2^LOGL splits into 1..3 Stockham stages of at most 32 points, larger first.
+__host__ __device__ constexpr int n_stages(int logl) { return logl <= 5 ? 1 : (logl <= 10 ? 2 : 3); }
+__host__ __device__ constexpr int stage_logr(int logl, int s) {
+    return logl / n_stages(logl) + (s < logl % n_stages(logl) ? 1 : 0);
+}
+__host__ __device__ constexpr int stage_logns(int logl, int s) {
+    return s == 0 ? 0 : stage_logns(logl, s - 1) + stage_logr(logl, s - 1);
+}
+// butterflies of the last (smallest-radix) stage = threads per column
+__host__ __device__ constexpr int max_bfly(int logl) { return 1 << (logl - stage_logr(logl, n_stages(logl) - 1)); }
+// odd smem row stride for T columns (bank spread for both thread mappings)
+__host__ __device__ constexpr int row_stride(int T) { return T == 1 ? 1 : ((T & 1) ? T : T + 1); }
+
+template <int LOGL, int S>
+struct Stage {
+    static constexpr int LR = stage_logr(LOGL, S), R = 1 << LR;
+    static constexpr int LNS = stage_logns(LOGL, S), NS = 1 << LNS;
+    static constexpr int NB = (1 << LOGL) >> LR;   // butterflies per column
 };
+
+// Stage S >= 1 input: v[r] = buf[(j + r NB) * TT + t] times the stage twiddle
+// e^{-2 pi i r (j mod NS) / (NS R)}
+template <int LOGL, int S, int TT>
+__device__ __forceinline__ void stage_load(float2* v, const float2* buf, int j, int t,
+                                           const float2* __restrict__ tw_tab) {
+    using St = Stage<LOGL, S>;
+#pragma unroll
+    for (int r = 0; r < St::R; r++) v[r] = buf[(j + r * St::NB) * TT + t];
+    if constexpr (S > 0) {
+        const int k = j & (St::NS - 1);
+        const float2* tw = tw_tab + (St::NS * St::R);
+#pragma unroll
+        for (int r = 1; r < St::R; r++) v[r] = cmul(v[r], __ldg(&tw[r * k]));
+    }
+}
+
+// Non-final stage output: buf[((j - k) R + k + r NS) * TT + t]
+template <int LOGL, int S, int TT>
+__device__ __forceinline__ void stage_store(const float2* v, float2* buf, int j, int t) {
+    using St = Stage<LOGL, S>;
+    const int k = j & (St::NS - 1);
+    const int base = (j - k) * St::R + k;
+#pragma unroll
+    for (int r = 0; r < St::R; r++) buf[(base + r * St::NS) * TT + t] = v[r];
+}
+
+// Runs the CTA FFT of T columns of length L.  fill(v, j, t, stride) produces
+// the first stage's R inputs x(j + r stride); out(v, j, t, stride) consumes
+// the last stage's R outputs X(j + r stride).  The last stage maps threads
+// j-fastest when LAST_JFAST (coalesced writes along the DFT index),
+// t-fastest otherwise.  Only columns t < tlim (<= T) are computed.
+template <int LOGL, int T, int NT, bool LAST_JFAST, class Fill, class Out>
+__device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ tw_tab, Fill& fill, Out& out,
+                                        int tlim) {
+    constexpr int NST = n_stages(LOGL);
+    constexpr int TT = row_stride(T);
+    const int tid = threadIdx.x;
+    {
+        using S0 = Stage<LOGL, 0>;
+        constexpr bool last = (NST == 1);
+        const int t = (last && LAST_JFAST) ? tid / S0::NB : tid % T;
+        const int j = (last && LAST_JFAST) ? tid % S0::NB : tid / T;
+        float2 v[S0::R];
+        if (j < S0::NB && t < tlim) {
+            fill(v, j, t, S0::NB);
+            dft<S0::R>(v);
+            if constexpr (last) out(v, j, t, S0::NB);
+            else stage_store<LOGL, 0, TT>(v, buf, j, t);
+        }
+    }
+    if constexpr (NST >= 2) {
+        __syncthreads();
+        using S1 = Stage<LOGL, 1>;
+        constexpr bool last = (NST == 2);
+        const int t = (last && LAST_JFAST) ? tid / S1::NB : tid % T;
+        const int j = (last && LAST_JFAST) ? tid % S1::NB : tid / T;
+        float2 v[S1::R];
+        const bool act = j < S1::NB && t < tlim;
+        if (act) {
+            stage_load<LOGL, 1, TT>(v, buf, j, t, tw_tab);
+            dft<S1::R>(v);
+        }
+        if constexpr (last) {
+            if (act) out(v, j, t, S1::NB);
+        } else {
+            __syncthreads();
+            if (act) stage_store<LOGL, 1, TT>(v, buf, j, t);
+        }
+    }
+    if constexpr (NST >= 3) {
+        __syncthreads();
+        using S2 = Stage<LOGL, 2>;
+        const int t = LAST_JFAST ? tid / S2::NB : tid % T;
+        const int j = LAST_JFAST ? tid % S2::NB : tid / T;
+        if (j < S2::NB && t < tlim) {
+            float2 v[S2::R];
+            stage_load<LOGL, 2, TT>(v, buf, j, t, tw_tab);
+            dft<S2::R>(v);
+            out(v, j, t, S2::NB);
+        }
+    }
+}
 
 // ------------------------------------------------------------ block reduce
 
@@ -253,145 +321,292 @@ __device__ __forceinline__ void block_sum2(float a, float b, double* out_a, doub
     }
 }
 
-// ------------------------------------------------------------ final pass
+// ------------------------------------------------------- output to W rows
 
-// Tile = T_eff consecutive columns d of one job; computes the B-point DFTs
-// over b and writes X(d + A c) for c < B.
-template <int LOGB, int T, int NT, int SRC, int SINK>
-__global__ void __launch_bounds__(NT) k_final(Params p, const Job* __restrict__ jobs,
-                                              const int32_t* __restrict__ tile_job) {
-    constexpr int B = 1 << LOGB;
-    constexpr int PAD = (T < 16 && T > 1) ? 1 : 0;
-    using FFT = SmemFFT<LOGB, T, NT, true, PAD>;
-    extern __shared__ float2 smem[];
-    float2* X = smem;
-    float2* Zs = smem + B * (T + PAD);
-    __shared__ double red[2 * ((NT + 31) / 32)];
+// Stores X(d + A c) for the last stage's outputs c = j + r * cstride; crops
+// n >= N; accumulates |W|^2 per row.
+struct WOut {
+    const Params* p;
+    float* r0;           // GDW rows (re -> r0, im -> r1)
+    float* r1;
+    float2* rc;          // Morlet row
+    int d0;
+    float pw0, pw1;
+    template <int R>
+    __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int cstride) {
+        const int d = d0 + t;
+        const int N = (int)p->N;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int n = d + p->A * (j + r * cstride);
+            if (n < N) {
+                if (rc) {
+                    rc[n] = v[r];
+                    pw0 = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, pw0));
+                } else {
+                    r0[n] = v[r].x;
+                    pw0 = fmaf(v[r].x, v[r].x, pw0);
+                    if (r1) {
+                        r1[n] = v[r].y;
+                        pw1 = fmaf(v[r].y, v[r].y, pw1);
+                    }
+                }
+            }
+        }
+    }
+};
 
-    const int tile = blockIdx.x;
-    const int T_eff = p.T_eff;
-    Job J;
-    int d0 = 0;
-    if (SRC == SRC_BAND || SINK == SINK_W) {
-        int ji = tile_job ? __ldg(&tile_job[tile]) : p.job;
-        J = jobs[ji];
-        d0 = (tile - J.tile0) * T_eff;
+__device__ __forceinline__ WOut make_wout(const Params& p, const Job& J, int d0) {
+    WOut o;
+    o.p = &p;
+    o.d0 = d0;
+    o.pw0 = o.pw1 = 0.f;
+    if (p.wavelet == WAV_GDW) {
+        o.rc = nullptr;
+        o.r0 = (float*)p.W + (int64_t)J.g[0].row * p.N;
+        o.r1 = J.g[1].row >= 0 ? (float*)p.W + (int64_t)J.g[1].row * p.N : nullptr;
     } else {
-        d0 = tile * T_eff;
+        o.rc = (float2*)p.W + (int64_t)J.g[0].row * p.N;
+        o.r0 = o.r1 = nullptr;
     }
+    return o;
+}
 
-    if (SRC == SRC_BAND) {
-        for (int i = threadIdx.x; i < J.K; i += NT) Zs[i] = band_value(p, J, J.k_lo + i);
-        __syncthreads();
-        const int kend = J.k_lo + J.K;
-        for (int e = threadIdx.x; e < B * T; e += NT) {
-            int t = e % T, b = e / T;
-            if (t >= T_eff) continue;
-            uint32_t d = (uint32_t)(d0 + t);
-            int first = J.k_lo + (((b - J.k_lo) % B) + B) % B;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int k = first; k < kend; k += B) {
-                uint32_t j = ((uint32_t)k * d) & (uint32_t)(p.M - 1);
-                float2 z = Zs[k - J.k_lo];
-                float2 w = tw_m(p, j);
-                acc = cadd(acc, cmul(z, w));
-            }
-            X[FFT::addr(b, t)] = acc;
-        }
-    } else if (SRC == SRC_Y) {
-        for (int e = threadIdx.x; e < B * T; e += NT) {
-            int t = e % T, b = e / T;
-            if (t >= T_eff) continue;
-            X[FFT::addr(b, t)] = p.Y[(int64_t)b * p.A + d0 + t];
-        }
-    } else {  // SRC_SIGNAL: whole transform in one tile (A = 1, T_eff = 1)
-        for (int b = threadIdx.x; b < B; b += NT) X[FFT::addr(b, 0)] = make_float2(load_signal(p, b), 0.f);
-    }
-    __syncthreads();
-    FFT::run(X, T_eff, p.tw_L);
-
-    if (SINK == SINK_FWD) {
-        const int half = p.M >> 1;
-        for (int e = threadIdx.x; e < B * T; e += NT) {
-            int t = e % T, c = e / T;
-            if (t >= T_eff) continue;
-            int n = d0 + t + p.A * c;
-            if (n <= half) {
-                float2 v = X[FFT::addr(c, t)];
-                p.Fp_out[n] = make_float2(v.x, -v.y);
-            }
-        }
-        return;
-    }
-
-    // SINK_W: crop to n < N, store, accumulate |W|^2
-    float pw0 = 0.f, pw1 = 0.f;
-    const bool two = (p.wavelet == WAV_GDW) && (J.g[1].row >= 0);
-    float* Wr0 = (float*)p.W + (int64_t)J.g[0].row * p.N;
-    float* Wr1 = two ? (float*)p.W + (int64_t)J.g[1].row * p.N : nullptr;
-    float2* Wc = (float2*)p.W + (int64_t)J.g[0].row * p.N;
-    for (int e = threadIdx.x; e < B * T; e += NT) {
-        int t = e % T, c = e / T;
-        if (t >= T_eff) continue;
-        int64_t n = (int64_t)d0 + t + (int64_t)p.A * c;
-        if (n >= p.N) continue;
-        float2 v = X[FFT::addr(c, t)];
-        if (p.wavelet == WAV_GDW) {
-            Wr0[n] = v.x;
-            pw0 = fmaf(v.x, v.x, pw0);
-            if (two) { Wr1[n] = v.y; pw1 = fmaf(v.y, v.y, pw1); }
-        } else {
-            Wc[n] = v;
-            pw0 = fmaf(v.x, v.x, fmaf(v.y, v.y, pw0));
-        }
-    }
-    if (p.do_power) {
-        double s0, s1;
-        block_sum2<NT>(pw0, pw1, &s0, &s1, red);
-        if (threadIdx.x == 0) {
-            int slot = tile - J.tile0;
-            p.partials[J.g[0].part_off + slot] = s0;
-            if (two) p.partials[J.g[1].part_off + slot] = s1;
-        }
+template <int NT>
+__device__ __forceinline__ void write_partials(const Params& p, const Job& J, const WOut& o, int slot, double* red) {
+    if (!p.do_power) return;
+    double s0, s1;
+    block_sum2<NT>(o.pw0, o.pw1, &s0, &s1, red);
+    if (threadIdx.x == 0) {
+        p.partials[J.g[0].part_off + slot] = s0;
+        if (J.g[1].row >= 0 && p.wavelet == WAV_GDW) p.partials[J.g[1].part_off + slot] = s1;
     }
 }
 
-// ------------------------------------------------------------ pass 1
+// ------------------------------------------------------------ band kernel
 
-// Tile = T1 consecutive columns b; A-point DFT over a of x(b + B a), then the
-// twiddle e^{-2 pi i b d / M}; writes Y[b][d].
-template <int LOGA, int T1, int NT, int MODE>
-__global__ void __launch_bounds__(NT) k_pass1(Params p, const Job* __restrict__ jobs) {
-    constexpr int A = 1 << LOGA;
-    constexpr int PAD = 1;
-    using FFT = SmemFFT<LOGA, T1, NT, false, PAD>;
-    extern __shared__ float2 smem[];
-    float2* X = smem;
-    const int B = p.M >> LOGA;
-    const int b0 = blockIdx.x * T1;
-    const int half = p.M >> 1;
-    Job J;
-    if (MODE == P1_BAND) J = jobs[p.job];
-
-    for (int e = threadIdx.x; e < A * T1; e += NT) {
-        int t = e % T1, a = e / T1;
-        int k = b0 + t + B * a;                 // unsigned bin in [0, M)
-        float2 v = make_float2(0.f, 0.f);
-        if (MODE == P1_BAND) {
-            int ks = k <= half ? k : k - p.M;
-            if (ks >= J.k_lo && ks < J.k_lo + J.K) v = band_value(p, J, ks);
-        } else {
-            v.x = load_signal(p, k);
+// First-stage fill of a band tile.  The sub-problem has length Mp = M / mult
+// and its band is [kb, kb + L); Zs[i] holds z(kb + i) (zero past the band).
+// Slot rho of the first stage takes k_rho = kb + ((rho - kb) mod L) and
+// x(rho) = Zs[k_rho - kb] e^{-2 pi i k_rho d / Mp}.  For the slots
+// rho = j + r NB0 of one thread, k_rho grows by NB0 per slot except once,
+// where it wraps by -L, so the twiddle is carried by a recurrence (at most
+// 32 steps) from one exact anchor.
+template <int LOGL>
+struct BandFill {
+    const Params* p;
+    const float2* Zs;
+    int kb;          // first bin of the band (sub-problem index space)
+    uint32_t mult;   // e^{-2 pi i x / Mp} = e^{-2 pi i (x mult) / M}
+    int d0;
+    template <int R>
+    __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int nb) {
+        constexpr int L = 1 << LOGL;
+        const uint32_t d = (uint32_t)(d0 + t);
+        const uint32_t mask = (uint32_t)(p->M - 1);
+        const int e0 = (j - kb) & (L - 1);
+        const int r_w = (L - e0 + nb - 1) / nb;          // slot index of the wrap (>= R: none)
+        const uint32_t k0 = (uint32_t)(kb + e0);
+        float2 w = tw_m(*p, (k0 * d * mult) & mask);
+        const float2 g = tw_m(*p, ((uint32_t)nb * d * mult) & mask);
+        const float2 gw = tw_m(*p, ((uint32_t)(nb - L) * d * mult) & mask);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            v[r] = cmul(Zs[(e0 + r * nb) & (L - 1)], w);
+            if (r + 1 < R) w = cmul(w, (r + 1 == r_w) ? gw : g);
         }
-        X[FFT::addr(a, t)] = v;
+    }
+};
+
+template <int LOGL, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_band(Params p) {
+    constexpr int L = 1 << LOGL;
+    constexpr int NT = T * max_bfly(LOGL);
+    extern __shared__ float2 smem[];
+    float2* Zs = smem;
+    float2* buf = smem + L;
+    __shared__ double red[2 * ((NT + 31) / 32)];
+
+    const int tile = blockIdx.x;
+    const Job J = p.jobs[__ldg(&p.tile_job[tile])];
+    const int d0 = (tile - J.tile0) * T;
+    for (int i = threadIdx.x; i < L; i += NT)
+        Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
+    __syncthreads();
+    BandFill<LOGL> fill{&p, Zs, J.k_lo, 1u, d0};
+    WOut out = make_wout(p, J, d0);
+    cta_fft<LOGL, T, NT, false>(buf, p.tw_tab, fill, out, min(T, p.A - d0));
+    write_partials<NT>(p, J, out, tile - J.tile0, red);
+}
+
+// ------------------------------------------------------------ wide pass 1
+
+// x(a) = Z(b + L a) for column b (zero outside the band) ...
+struct Wide1Fill {
+    const Params* p;
+    const Job* J;
+    int b0, L;
+    template <int R>
+    __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
+        const int half = p->M >> 1;
+        const int kend = J->k_lo + J->K;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int k = b0 + t + L * (j + r * stride);      // unsigned bin in [0, M)
+            const int ks = k <= half ? k : k - p->M;
+            v[r] = (ks >= J->k_lo && ks < kend) ? band_value(*p, *J, ks) : make_float2(0.f, 0.f);
+        }
+    }
+};
+
+// ... and Y[b][d] = e^{-2 pi i b d / M} * (A-point DFT)(d).  Column layout:
+// full pass 1 (COLS_B): the tile's columns are b0 + t and d = c; pruned pass
+// 1: one column b, the tile's columns are d1 = d0 + t and d = d1 + A1 c.
+// The twiddle over the R outputs of a thread is a recurrence from one anchor.
+template <bool COLS_B>
+struct YOut {
+    const Params* p;
+    float2* Y;
+    int b0, d0, A, A1;
+    template <int R>
+    __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int stride) {
+        const uint32_t b = (uint32_t)(COLS_B ? b0 + t : b0);
+        const uint32_t d1 = (uint32_t)(COLS_B ? 0 : d0 + t);
+        const uint32_t mask = (uint32_t)(p->M - 1);
+        float2* row = Y + (int64_t)b * A;
+        const uint32_t dj = d1 + (uint32_t)A1 * (uint32_t)j;
+        float2 w = tw_m(*p, (b * dj) & mask);
+        const float2 g = tw_m(*p, (b * (uint32_t)A1 * (uint32_t)stride) & mask);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            row[dj + (uint32_t)A1 * (uint32_t)(r * stride)] = cmul(v[r], w);
+            if (r + 1 < R) w = cmul(w, g);
+        }
+    }
+};
+
+// grid (L / T, jobs in batch): T columns b of the A-point DFTs of one job
+template <int LOGA, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGA)) k_wide1(Params p) {
+    constexpr int NT = T * max_bfly(LOGA);
+    extern __shared__ float2 smem[];
+    const int L = p.M >> LOGA;
+    const Job J = p.jobs[p.job0 + blockIdx.y];
+    const int b0 = blockIdx.x * T;
+    Wide1Fill fill{&p, &J, b0, L};
+    YOut<true> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b0, 0, 1 << LOGA, 1};
+    cta_fft<LOGA, T, NT, true>(smem, p.tw_tab, fill, out, min(T, L - b0));
+}
+
+// Pruned pass 1: column b only holds the band bins k = b mod L, i.e. the
+// sub-band a in [a0, a0 + P_b) of the A-point problem (k = b + L a), so its
+// A-point DFT is itself a band tile of L1 >= P_b points over A1 = A / L1
+// columns d1 (d = d1 + A1 c1).  grid (L * tiles_per_b, jobs in batch).
+template <int LOGL1, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGL1)) k_wide1p(Params p, int L, int tiles_per_b) {
+    constexpr int L1 = 1 << LOGL1;
+    constexpr int NT = T * max_bfly(LOGL1);
+    extern __shared__ float2 smem[];
+    float2* Zs = smem;
+    float2* buf = smem + L1;
+    const Job J = p.jobs[p.job0 + blockIdx.y];
+    const int b = blockIdx.x / tiles_per_b;
+    const int d0 = (blockIdx.x - b * tiles_per_b) * T;
+    const int A = p.M / L;
+    const int A1 = A >> LOGL1;
+    const int kb0 = J.k_lo + ((b - J.k_lo) & (L - 1));      // first band bin = b mod L
+    const int khi = J.k_lo + J.K - 1;
+    const int a0 = (kb0 - b) / L;                             // exact: kb0 = b (mod L)
+    for (int i = threadIdx.x; i < L1; i += NT) {
+        const int k = kb0 + L * i;
+        Zs[i] = k <= khi ? band_value(p, J, k) : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    FFT::run(X, T1, p.tw_L);
-    for (int e = threadIdx.x; e < A * T1; e += NT) {
-        int d = e % A, t = e / A;
-        uint32_t b = (uint32_t)(b0 + t);
-        float2 v = cmul(X[FFT::addr(d, t)], tw_m(p, (b * (uint32_t)d) & (uint32_t)(p.M - 1)));
-        p.Y[(int64_t)b * A + d] = v;
+    BandFill<LOGL1> fill{&p, Zs, a0, (uint32_t)L, d0};
+    YOut<false> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b, d0, A, A1};
+    cta_fft<LOGL1, T, NT, false>(buf, p.tw_tab, fill, out, min(T, A1 - d0));
+}
+
+// ------------------------------------------------------------ wide pass 2
+
+// x(b) = Y[b][d0 + t]
+struct YFill {
+    const float2* Y;
+    int A, d0;
+    template <int R>
+    __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = Y[(int64_t)(j + r * stride) * A + d0 + t];
+    }
+};
+
+// grid (A / T, jobs in batch): T columns d of the L-point DFTs over b
+template <int LOGL, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_wide2(Params p) {
+    constexpr int NT = T * max_bfly(LOGL);
+    extern __shared__ float2 smem[];
+    __shared__ double red[2 * ((NT + 31) / 32)];
+    const Job J = p.jobs[p.job0 + blockIdx.y];
+    const int d0 = blockIdx.x * T;
+    YFill fill{p.Y + (int64_t)blockIdx.y * p.M, p.A, d0};
+    WOut out = make_wout(p, J, d0);
+    cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
+    write_partials<NT>(p, J, out, blockIdx.x, red);
+}
+
+// ------------------------------------------------------------ forward
+
+// x(a) = f(b + L a) (zero past N)
+struct SigFill {
+    const Params* p;
+    int b0, L;
+    template <int R>
+    __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = make_float2(load_signal(*p, b0 + t + L * (j + r * stride)), 0.f);
+    }
+};
+
+// F(n) = conj X(n) for n = d0 + t + A c <= M/2 (the forward uses the paper's
+// e^{+} sign: sum_n f(n) e^{+2 pi i m n / M} = conj of the e^{-} DFT of real f)
+struct FOut {
+    float2* F;
+    int A, d0, half;
+    template <int R>
+    __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int stride) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int n = d0 + t + A * (j + r * stride);
+            if (n <= half) F[n] = make_float2(v[r].x, -v[r].y);
+        }
+    }
+};
+
+// pass 1 of the forward: grid L / T, A-point DFTs of the columns b
+template <int LOGA, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGA)) k_fwd1(Params p) {
+    constexpr int NT = T * max_bfly(LOGA);
+    extern __shared__ float2 smem[];
+    const int L = p.M >> LOGA;
+    const int b0 = blockIdx.x * T;
+    SigFill fill{&p, b0, L};
+    YOut<true> out{&p, p.Y, b0, 0, 1 << LOGA, 1};
+    cta_fft<LOGA, T, NT, true>(smem, p.tw_tab, fill, out, min(T, L - b0));
+}
+
+// pass 2 of the forward (or the whole forward when A = 1): grid A / T
+template <int LOGL, int T>
+__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_fwd2(Params p) {
+    constexpr int NT = T * max_bfly(LOGL);
+    extern __shared__ float2 smem[];
+    const int d0 = blockIdx.x * T;
+    FOut out{p.Fp_out, p.A, d0, p.M >> 1};
+    if (p.A == 1) {
+        SigFill fill{&p, 0, 1};
+        cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, 1);
+    } else {
+        YFill fill{p.Y, p.A, d0};
+        cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
     }
 }
 
