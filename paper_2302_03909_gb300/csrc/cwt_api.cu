@@ -39,14 +39,18 @@ constexpr int wide1_T(int loga) { return band_T(loga); }
 constexpr int wide1p_T(int logl) { return band_T(logl) > 32 ? 32 : band_T(logl); }
 
 using KernFn = void (*)(Params);
-struct Entry { KernFn fn; int T, NT, logl; };
+struct Entry { KernFn fn; int T, NT, logl; int D = 1; };
 
-template <int LOGL, int T>
-Entry band_entry() { return {k_band<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+// tiles of T columns per CTA for the W-writing kernels
+constexpr int kBandD = 8;
+constexpr int kWide2D = 2;
+
+template <int LOGL, int T, bool CROP>
+Entry band_entry() { return {k_band<LOGL, T, kBandD, CROP>, T, T * max_bfly(LOGL), LOGL, kBandD}; }
 template <int LOGL, int T>
 Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
-template <int LOGL, int T>
-Entry wide2_entry() { return {k_wide2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T, bool CROP>
+Entry wide2_entry() { return {k_wide2<LOGL, T, kWide2D, CROP>, T, T * max_bfly(LOGL), LOGL, kWide2D}; }
 template <int LOGL, int T>
 Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 template <int LOGL, int T>
@@ -58,9 +62,10 @@ template <int LOGL, int T>
 EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 
 template <int... L>
-void fill_tables(Entry* band, Entry* wide1, Entry* fwd1, Entry* fwd_small, EntryP* wide1p,
+void fill_tables(Entry (*band)[2], Entry* wide1, Entry* fwd1, Entry* fwd_small, EntryP* wide1p,
                  std::integer_sequence<int, L...>) {
-    ((band[L + 1] = band_entry<L + 1, band_T(L + 1)>()), ...);
+    ((band[L + 1][0] = band_entry<L + 1, band_T(L + 1), false>()), ...);
+    ((band[L + 1][1] = band_entry<L + 1, band_T(L + 1), true>()), ...);
     ((wide1p[L + 1] = wide1p_entry<L + 1, wide1p_T(L + 1)>()), ...);
     ((wide1[L + 1] = wide1_entry<L + 1, wide1_T(L + 1)>()), ...);
     ((fwd1[L + 1] = fwd1_entry<L + 1, wide1_T(L + 1)>()), ...);
@@ -68,11 +73,11 @@ void fill_tables(Entry* band, Entry* wide1, Entry* fwd1, Entry* fwd_small, Entry
 }
 
 struct Tables {
-    Entry band[kLmaxLog + 1];
+    Entry band[kLmaxLog + 1][2];     // [log2 L][crop]
     Entry wide1[kLmaxLog + 1];
     Entry fwd1[kLmaxLog + 1];
     Entry fwd_small[kLmaxLog + 1];
-    Entry wide2[kLmaxLog + 1];
+    Entry wide2[kLmaxLog + 1][2];    // [log2 L][crop]
     Entry fwd2[kLmaxLog + 1];
     EntryP wide1p[kLmaxLog + 1];
     Tables() {
@@ -82,13 +87,18 @@ struct Tables {
         wide1[13] = wide1_entry<13, wide1_T(13)>();
         fwd1[12] = fwd1_entry<12, wide1_T(12)>();
         fwd1[13] = fwd1_entry<13, wide1_T(13)>();
-        band[12] = band_entry<12, band_T(12)>();
-        band[13] = band_entry<13, band_T(13)>();
+        band[12][0] = band_entry<12, band_T(12), false>();
+        band[12][1] = band_entry<12, band_T(12), true>();
+        band[13][0] = band_entry<13, band_T(13), false>();
+        band[13][1] = band_entry<13, band_T(13), true>();
         fwd_small[12] = fwd2_entry<12, 1>();
         fwd_small[13] = fwd2_entry<13, 1>();
-        wide2[10] = wide2_entry<10, band_T(10)>();
-        wide2[11] = wide2_entry<11, band_T(11)>();
-        wide2[12] = wide2_entry<12, band_T(12)>();
+        wide2[10][0] = wide2_entry<10, band_T(10), false>();
+        wide2[10][1] = wide2_entry<10, band_T(10), true>();
+        wide2[11][0] = wide2_entry<11, band_T(11), false>();
+        wide2[11][1] = wide2_entry<11, band_T(11), true>();
+        wide2[12][0] = wide2_entry<12, band_T(12), false>();
+        wide2[12][1] = wide2_entry<12, band_T(12), true>();
         fwd2[10] = fwd2_entry<10, band_T(10)>();
         fwd2[11] = fwd2_entry<11, band_T(11)>();
         fwd2[12] = fwd2_entry<12, band_T(12)>();
@@ -158,6 +168,7 @@ struct cwt_plan {
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
     int wide_logl = 0, wide_loga = 0, wide_G = 0;
     int fwd_small = 0;
+    int crop = 0;                         // N < M: drop the padded outputs
     int64_t n_partials = 0;
     std::vector<int32_t> part_off, part_cnt;
     int64_t n_band_jobs = 0;
@@ -181,6 +192,12 @@ struct cwt_plan {
     // cwt_wavelet_power scratch
     double* d_pw_partials = nullptr;
     int64_t pw_chunks = 0;
+
+    // band groups run on side streams forked from the call's stream
+    static constexpr int kSide = 2;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kSide] = {};
 
     // timing hook (cwt_plan_set_timing)
     struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
@@ -242,6 +259,11 @@ void free_plan(cwt_plan* p) {
     release_events(p);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     p->ev_pool.clear();
+    for (int i = 0; i < cwt_plan::kSide; i++) {
+        if (p->side[i]) cudaStreamDestroy(p->side[i]);
+        if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials};
@@ -351,8 +373,8 @@ cwt_status build_plan(cwt_plan* p) {
         cwt_plan::BandGroup g;
         g.logl = ll;
         const int64_t A = M >> ll;
-        const int T = tb.band[ll].T;
-        const int per_job = (int)((A + T - 1) / T);
+        const int T = tb.band[ll][0].T, D = tb.band[ll][0].D;
+        const int per_job = (int)((A + (int64_t)T * D - 1) / ((int64_t)T * D));
         g.ntiles = 0;
         g.tj_off = tile_job.size();
         g.bytes = 0;
@@ -370,8 +392,8 @@ cwt_status build_plan(cwt_plan* p) {
     p->n_band_jobs = (int64_t)p->jobs.size();
     if (!wide.empty()) {
         const int64_t A = M >> p->wide_logl;
-        const int T2 = tb.wide2[p->wide_logl].T;
-        const int ntiles2 = (int)((A + T2 - 1) / T2);
+        const int T2 = tb.wide2[p->wide_logl][0].T, D2 = tb.wide2[p->wide_logl][0].D;
+        const int ntiles2 = (int)((A + (int64_t)T2 * D2 - 1) / ((int64_t)T2 * D2));
         p->wide_G = (int)std::max<int64_t>(1, (int64_t)(kWideBatchBytes / ((size_t)M * sizeof(float2))));
         const int L = 1 << p->wide_logl;
         for (size_t i = 0; i < wide.size(); i++) {
@@ -395,6 +417,7 @@ cwt_status build_plan(cwt_plan* p) {
     }
     p->n_partials = nparts;
     p->fwd_small = small;
+    p->crop = p->N < M;
     p->fwd_in_bytes = (double)p->N * (p->opts.input_dtype == CWT_INPUT_F64 ? 8.0 : 4.0);
     p->fwd_out_bytes = 8.0 * (double)(M / 2 + 1);
 
@@ -535,19 +558,35 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
             return st;
     }
 
-    // 2. band scales, one launch per DFT length
-    for (const auto& g : p->groups) {
-        const Entry& e = tb.band[g.logl];
+    // 2. band scales, one launch per DFT length, on side streams forked after the
+    //    forward transform (they only read F); the wide batches below stay on the
+    //    call's stream because they share the intermediate Y
+    const bool fork = !p->groups.empty() && !p->wide.empty();
+    if (fork) {
+        if (!p->ev_fork) {
+            CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+            for (int i = 0; i < cwt_plan::kSide; i++) {
+                CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
+                CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
+            }
+        }
+        CWT_CUDA(p, cudaEventRecord(p->ev_fork, s));
+        for (int i = 0; i < cwt_plan::kSide; i++) CWT_CUDA(p, cudaStreamWaitEvent(p->side[i], p->ev_fork, 0));
+    }
+    for (size_t gi = 0; gi < p->groups.size(); gi++) {
+        const auto& g = p->groups[gi];
+        const Entry& e = tb.band[g.logl][p->crop];
         Params Q = P;
         Q.A = (int32_t)(p->M >> g.logl);
         Q.tile_job = p->d_tile_job + g.tj_off;
         size_t smem = (size_t)(1 << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
-        if ((st = launch(p, e, dim3(g.ntiles), smem, Q, s, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
+        cudaStream_t gs = fork ? p->side[gi % cwt_plan::kSide] : s;
+        if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
     }
 
     // 3. wide scales in L2-sized batches: pass 1 (A-point DFTs + twiddle) then pass 2
     for (const auto& wb : p->wide) {
-        const Entry& e2 = tb.wide2[p->wide_logl];
+        const Entry& e2 = tb.wide2[p->wide_logl][p->crop];
         const int L = 1 << p->wide_logl;
         Params Q = P;
         Q.job0 = wb.job0;
@@ -571,9 +610,16 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
-        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T, wb.count), stage_smem(p->wide_logl, e2.T), Q, s,
+        if ((st = launch(p, e2, dim3((Q.A + e2.T * e2.D - 1) / (e2.T * e2.D), wb.count), stage_smem(p->wide_logl, e2.T), Q, s,
                          CWT_KCLASS_WIDE2, wb.out_bytes)) != CWT_OK)
             return st;
+    }
+
+    if (fork) {
+        for (int i = 0; i < cwt_plan::kSide; i++) {
+            CWT_CUDA(p, cudaEventRecord(p->ev_join[i], p->side[i]));
+            CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i], 0));
+        }
     }
 
     // 4. power spectrum: fixed-order reduction of the per-tile partials

@@ -197,32 +197,37 @@ __device__ __forceinline__ void dft(float2* v) {
 
 // ------------------------------------------------------- CTA-level FFT plan
 
-// L = 2^LOGL splits into 1..3 Stockham stages of at most 32 points, larger first.
-__host__ __device__ constexpr int n_stages(int logl) { return logl <= 5 ? 1 : (logl <= 10 ? 2 : 3); }
-__host__ __device__ constexpr int stage_logr(int logl, int s) {
-    return logl / n_stages(logl) + (s < logl % n_stages(logl) ? 1 : 0);
+// L = 2^LOGL splits into ceil(LOGL / MAXLR) Stockham stages of at most
+// 2^MAXLR points each (larger radices first).  MAXLR = 5 keeps 32 complex
+// values per thread; MAXLR = 4 halves the registers per thread for higher
+// occupancy at the cost of more shared-memory exchanges.
+__host__ __device__ constexpr int n_stages(int logl, int maxlr = 5) { return (logl + maxlr - 1) / maxlr; }
+__host__ __device__ constexpr int stage_logr(int logl, int s, int maxlr = 5) {
+    return logl / n_stages(logl, maxlr) + (s < logl % n_stages(logl, maxlr) ? 1 : 0);
 }
-__host__ __device__ constexpr int stage_logns(int logl, int s) {
-    return s == 0 ? 0 : stage_logns(logl, s - 1) + stage_logr(logl, s - 1);
+__host__ __device__ constexpr int stage_logns(int logl, int s, int maxlr = 5) {
+    return s == 0 ? 0 : stage_logns(logl, s - 1, maxlr) + stage_logr(logl, s - 1, maxlr);
 }
 // butterflies of the last (smallest-radix) stage = threads per column
-__host__ __device__ constexpr int max_bfly(int logl) { return 1 << (logl - stage_logr(logl, n_stages(logl) - 1)); }
+__host__ __device__ constexpr int max_bfly(int logl, int maxlr = 5) {
+    return 1 << (logl - stage_logr(logl, n_stages(logl, maxlr) - 1, maxlr));
+}
 // odd smem row stride for T columns (bank spread for both thread mappings)
 __host__ __device__ constexpr int row_stride(int T) { return T == 1 ? 1 : ((T & 1) ? T : T + 1); }
 
-template <int LOGL, int S>
+template <int LOGL, int S, int MAXLR = 5>
 struct Stage {
-    static constexpr int LR = stage_logr(LOGL, S), R = 1 << LR;
-    static constexpr int LNS = stage_logns(LOGL, S), NS = 1 << LNS;
+    static constexpr int LR = stage_logr(LOGL, S, MAXLR), R = 1 << LR;
+    static constexpr int LNS = stage_logns(LOGL, S, MAXLR), NS = 1 << LNS;
     static constexpr int NB = (1 << LOGL) >> LR;   // butterflies per column
 };
 
 // Stage S >= 1 input: v[r] = buf[(j + r NB) * TT + t] times the stage twiddle
 // e^{-2 pi i r (j mod NS) / (NS R)}
-template <int LOGL, int S, int TT>
+template <int LOGL, int S, int TT, int MAXLR>
 __device__ __forceinline__ void stage_load(float2* v, const float2* buf, int j, int t,
                                            const float2* __restrict__ tw_tab) {
-    using St = Stage<LOGL, S>;
+    using St = Stage<LOGL, S, MAXLR>;
 #pragma unroll
     for (int r = 0; r < St::R; r++) v[r] = buf[(j + r * St::NB) * TT + t];
     if constexpr (S > 0) {
@@ -234,13 +239,37 @@ __device__ __forceinline__ void stage_load(float2* v, const float2* buf, int j, 
 }
 
 // Non-final stage output: buf[((j - k) R + k + r NS) * TT + t]
-template <int LOGL, int S, int TT>
+template <int LOGL, int S, int TT, int MAXLR>
 __device__ __forceinline__ void stage_store(const float2* v, float2* buf, int j, int t) {
-    using St = Stage<LOGL, S>;
+    using St = Stage<LOGL, S, MAXLR>;
     const int k = j & (St::NS - 1);
     const int base = (j - k) * St::R + k;
 #pragma unroll
     for (int r = 0; r < St::R; r++) buf[(base + r * St::NS) * TT + t] = v[r];
+}
+
+// Middle stage S (0 < S < NST - 1): load, twiddle, DFT, exchange.
+template <int LOGL, int S, int T, int TT, int MAXLR>
+__device__ __forceinline__ void cta_mid_stage(float2* buf, const float2* __restrict__ tw_tab, int tlim) {
+    using St = Stage<LOGL, S, MAXLR>;
+    __syncthreads();
+    const int t = threadIdx.x % T, j = threadIdx.x / T;
+    float2 v[St::R];
+    const bool act = j < St::NB && t < tlim;
+    if (act) {
+        stage_load<LOGL, S, TT, MAXLR>(v, buf, j, t, tw_tab);
+        dft<St::R>(v);
+    }
+    __syncthreads();
+    if (act) stage_store<LOGL, S, TT, MAXLR>(v, buf, j, t);
+}
+
+template <int LOGL, int S, int NST, int T, int TT, int MAXLR>
+__device__ __forceinline__ void cta_mid_stages(float2* buf, const float2* __restrict__ tw_tab, int tlim) {
+    if constexpr (S < NST - 1) {
+        cta_mid_stage<LOGL, S, T, TT, MAXLR>(buf, tw_tab, tlim);
+        cta_mid_stages<LOGL, S + 1, NST, T, TT, MAXLR>(buf, tw_tab, tlim);
+    }
 }
 
 // Runs the CTA FFT of T columns of length L.  fill(v, j, t, stride) produces
@@ -248,14 +277,14 @@ __device__ __forceinline__ void stage_store(const float2* v, float2* buf, int j,
 // the last stage's R outputs X(j + r stride).  The last stage maps threads
 // j-fastest when LAST_JFAST (coalesced writes along the DFT index),
 // t-fastest otherwise.  Only columns t < tlim (<= T) are computed.
-template <int LOGL, int T, int NT, bool LAST_JFAST, class Fill, class Out>
+template <int LOGL, int T, int NT, bool LAST_JFAST, int MAXLR, class Fill, class Out>
 __device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ tw_tab, Fill& fill, Out& out,
                                         int tlim) {
-    constexpr int NST = n_stages(LOGL);
+    constexpr int NST = n_stages(LOGL, MAXLR);
     constexpr int TT = row_stride(T);
     const int tid = threadIdx.x;
     {
-        using S0 = Stage<LOGL, 0>;
+        using S0 = Stage<LOGL, 0, MAXLR>;
         constexpr bool last = (NST == 1);
         const int t = (last && LAST_JFAST) ? tid / S0::NB : tid % T;
         const int j = (last && LAST_JFAST) ? tid % S0::NB : tid / T;
@@ -264,38 +293,20 @@ __device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ 
             fill(v, j, t, S0::NB);
             dft<S0::R>(v);
             if constexpr (last) out(v, j, t, S0::NB);
-            else stage_store<LOGL, 0, TT>(v, buf, j, t);
+            else stage_store<LOGL, 0, TT, MAXLR>(v, buf, j, t);
         }
     }
     if constexpr (NST >= 2) {
+        cta_mid_stages<LOGL, 1, NST, T, TT, MAXLR>(buf, tw_tab, tlim);
         __syncthreads();
-        using S1 = Stage<LOGL, 1>;
-        constexpr bool last = (NST == 2);
-        const int t = (last && LAST_JFAST) ? tid / S1::NB : tid % T;
-        const int j = (last && LAST_JFAST) ? tid % S1::NB : tid / T;
-        float2 v[S1::R];
-        const bool act = j < S1::NB && t < tlim;
-        if (act) {
-            stage_load<LOGL, 1, TT>(v, buf, j, t, tw_tab);
-            dft<S1::R>(v);
-        }
-        if constexpr (last) {
-            if (act) out(v, j, t, S1::NB);
-        } else {
-            __syncthreads();
-            if (act) stage_store<LOGL, 1, TT>(v, buf, j, t);
-        }
-    }
-    if constexpr (NST >= 3) {
-        __syncthreads();
-        using S2 = Stage<LOGL, 2>;
-        const int t = LAST_JFAST ? tid / S2::NB : tid % T;
-        const int j = LAST_JFAST ? tid % S2::NB : tid / T;
-        if (j < S2::NB && t < tlim) {
-            float2 v[S2::R];
-            stage_load<LOGL, 2, TT>(v, buf, j, t, tw_tab);
-            dft<S2::R>(v);
-            out(v, j, t, S2::NB);
+        using SL = Stage<LOGL, NST - 1, MAXLR>;
+        const int t = LAST_JFAST ? tid / SL::NB : tid % T;
+        const int j = LAST_JFAST ? tid % SL::NB : tid / T;
+        if (j < SL::NB && t < tlim) {
+            float2 v[SL::R];
+            stage_load<LOGL, NST - 1, TT, MAXLR>(v, buf, j, t, tw_tab);
+            dft<SL::R>(v);
+            out(v, j, t, SL::NB);
         }
     }
 }
@@ -323,8 +334,10 @@ __device__ __forceinline__ void block_sum2(float a, float b, double* out_a, doub
 
 // ------------------------------------------------------- output to W rows
 
-// Stores X(d + A c) for the last stage's outputs c = j + r * cstride; crops
-// n >= N; accumulates |W|^2 per row.
+// Stores X(d + A c) for the last stage's outputs c = j + r * cstride
+// (d = d0 + t); with CROP, outputs n >= N (zero-boundary padding) are
+// dropped.  Accumulates |W|^2 per row.
+template <bool CROP>
 struct WOut {
     const Params* p;
     float* r0;           // GDW rows (re -> r0, im -> r1)
@@ -334,20 +347,29 @@ struct WOut {
     float pw0, pw1;
     template <int R>
     __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int cstride) {
-        const int d = d0 + t;
+        const int n0 = d0 + t + p->A * j;
+        const int step = p->A * cstride;
         const int N = (int)p->N;
+        if (rc) {
+            float2* q = rc + n0;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int n = d + p->A * (j + r * cstride);
-            if (n < N) {
-                if (rc) {
-                    rc[n] = v[r];
+            for (int r = 0; r < R; r++) {
+                if (!CROP || n0 + r * step < N) {
+                    q[r * step] = v[r];
                     pw0 = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, pw0));
-                } else {
-                    r0[n] = v[r].x;
+                }
+            }
+        } else {
+            float* q0 = r0 + n0;
+            float* q1 = r1 ? r1 + n0 : r0 + n0;
+            const bool two = r1 != nullptr;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                if (!CROP || n0 + r * step < N) {
+                    q0[r * step] = v[r].x;
                     pw0 = fmaf(v[r].x, v[r].x, pw0);
-                    if (r1) {
-                        r1[n] = v[r].y;
+                    if (two) {
+                        q1[r * step] = v[r].y;
                         pw1 = fmaf(v[r].y, v[r].y, pw1);
                     }
                 }
@@ -356,8 +378,9 @@ struct WOut {
     }
 };
 
-__device__ __forceinline__ WOut make_wout(const Params& p, const Job& J, int d0) {
-    WOut o;
+template <bool CROP>
+__device__ __forceinline__ WOut<CROP> make_wout(const Params& p, const Job& J, int d0) {
+    WOut<CROP> o;
     o.p = &p;
     o.d0 = d0;
     o.pw0 = o.pw1 = 0.f;
@@ -372,8 +395,8 @@ __device__ __forceinline__ WOut make_wout(const Params& p, const Job& J, int d0)
     return o;
 }
 
-template <int NT>
-__device__ __forceinline__ void write_partials(const Params& p, const Job& J, const WOut& o, int slot, double* red) {
+template <int NT, class O>
+__device__ __forceinline__ void write_partials(const Params& p, const Job& J, const O& o, int slot, double* red) {
     if (!p.do_power) return;
     double s0, s1;
     block_sum2<NT>(o.pw0, o.pw1, &s0, &s1, red);
@@ -407,21 +430,34 @@ struct BandFill {
         const int e0 = (j - kb) & (L - 1);
         const int r_w = (L - e0 + nb - 1) / nb;          // slot index of the wrap (>= R: none)
         const uint32_t k0 = (uint32_t)(kb + e0);
-        float2 w = tw_m(*p, (k0 * d * mult) & mask);
+        // e^{-2 pi i k_r d / Mp} over the slots as CH interleaved recurrences
+        // (chain depth R / CH): w_{r + CH} = w_r g^CH, times e^{-2 pi i (-L) d / Mp}
+        // once when the chain crosses the wrap slot r_w
+        constexpr int CH = R >= 8 ? 4 : 1;
         const float2 g = tw_m(*p, ((uint32_t)nb * d * mult) & mask);
-        const float2 gw = tw_m(*p, ((uint32_t)(nb - L) * d * mult) & mask);
+        const float2 h = tw_m(*p, ((uint32_t)(-L) * d * mult) & mask);
+        float2 w[CH];
+        w[0] = tw_m(*p, (k0 * d * mult) & mask);
+#pragma unroll
+        for (int c = 1; c < CH; c++) w[c] = cmul(w[c - 1], c == r_w ? cmul(g, h) : g);
+        float2 gc = g;
+#pragma unroll
+        for (int c = 1; c < CH; c++) gc = cmul(gc, g);
+        const float2 gch = cmul(gc, h);
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            v[r] = cmul(Zs[(e0 + r * nb) & (L - 1)], w);
-            if (r + 1 < R) w = cmul(w, (r + 1 == r_w) ? gw : g);
+            v[r] = cmul(Zs[(e0 + r * nb) & (L - 1)], w[r % CH]);
+            if (r + CH < R) w[r % CH] = cmul(w[r % CH], (r < r_w && r + CH >= r_w) ? gch : gc);
         }
     }
 };
 
-template <int LOGL, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_band(Params p) {
+// One CTA handles D consecutive tiles of T columns of one job: the band
+// values, the job descriptor and the power reduction are paid once per CTA.
+template <int LOGL, int T, int D, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_band(Params p) {
     constexpr int L = 1 << LOGL;
-    constexpr int NT = T * max_bfly(LOGL);
+    constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L;
@@ -429,13 +465,64 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL)) k_band(Params p) {
 
     const int tile = blockIdx.x;
     const Job J = p.jobs[__ldg(&p.tile_job[tile])];
-    const int d0 = (tile - J.tile0) * T;
+    const int dbase = (tile - J.tile0) * T * D;
     for (int i = threadIdx.x; i < L; i += NT)
         Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
+    WOut<CROP> out = make_wout<CROP>(p, J, dbase);
+#pragma unroll 1
+    for (int q = 0; q < D; q++) {
+        const int d0 = dbase + q * T;
+        if (d0 >= p.A) break;
+        __syncthreads();
+        BandFill<LOGL> fill{&p, Zs, J.k_lo, 1u, d0};
+        out.d0 = d0;
+        cta_fft<LOGL, T, NT, false, MAXLR>(buf, p.tw_tab, fill, out, min(T, p.A - d0));
+    }
+    write_partials<NT>(p, J, out, tile - J.tile0, red);
+}
+
+// Single-stage band kernel (L <= 32) with D columns per thread: thread i of
+// the tile handles the columns d = d0 + i + NT q (q < D).  The first column's
+// inputs come from BandFill; each further column multiplies slot rho by the
+// per-job step sig[rho] = e^{-2 pi i k_rho NT / M} (a recurrence of at most
+// D - 1 steps per slot), so the band values and table anchors are paid once
+// per D columns.
+template <int LOGL, int NT, int D>
+__global__ void __launch_bounds__(NT) k_band1(Params p) {
+    constexpr int L = 1 << LOGL;
+    static_assert(LOGL <= 5, "single register stage");
+    __shared__ float2 Zs[L];
+    __shared__ float2 sig[L];
+    __shared__ double red[2 * ((NT + 31) / 32)];
+    const int tile = blockIdx.x;
+    const Job J = p.jobs[__ldg(&p.tile_job[tile])];
+    const int d0 = (tile - J.tile0) * NT * D;
+    const uint32_t mask = (uint32_t)(p.M - 1);
+    for (int i = threadIdx.x; i < L; i += NT) {
+        Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
+        const int krho = J.k_lo + ((i - J.k_lo) & (L - 1));   // band bin of residue rho = i
+        sig[i] = tw_m(p, ((uint32_t)krho * (uint32_t)NT) & mask);
+    }
     __syncthreads();
     BandFill<LOGL> fill{&p, Zs, J.k_lo, 1u, d0};
-    WOut out = make_wout(p, J, d0);
-    cta_fft<LOGL, T, NT, false>(buf, p.tw_tab, fill, out, min(T, p.A - d0));
+    WOut<true> out = make_wout<true>(p, J, d0);
+    float2 x[L];
+    const int t0 = threadIdx.x;
+    if (d0 + t0 < p.A) fill(x, 0, t0, 1);
+#pragma unroll 1
+    for (int q = 0; q < D; q++) {
+        const int t = t0 + NT * q;
+        if (d0 + t >= p.A) break;
+        if (q > 0) {
+#pragma unroll
+            for (int r = 0; r < L; r++) x[r] = cmul(x[r], sig[r]);
+        }
+        float2 v[L];
+#pragma unroll
+        for (int r = 0; r < L; r++) v[r] = x[r];
+        dft<L>(v);
+        out(v, 0, t, 1);
+    }
     write_partials<NT>(p, J, out, tile - J.tile0, red);
 }
 
@@ -475,37 +562,44 @@ struct YOut {
         const uint32_t mask = (uint32_t)(p->M - 1);
         float2* row = Y + (int64_t)b * A;
         const uint32_t dj = d1 + (uint32_t)A1 * (uint32_t)j;
-        float2 w = tw_m(*p, (b * dj) & mask);
+        constexpr int CH = R >= 8 ? 4 : 1;                 // interleaved recurrences
         const float2 g = tw_m(*p, (b * (uint32_t)A1 * (uint32_t)stride) & mask);
+        float2 w[CH];
+        w[0] = tw_m(*p, (b * dj) & mask);
+#pragma unroll
+        for (int c = 1; c < CH; c++) w[c] = cmul(w[c - 1], g);
+        float2 gc = g;
+#pragma unroll
+        for (int c = 1; c < CH; c++) gc = cmul(gc, g);
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            row[dj + (uint32_t)A1 * (uint32_t)(r * stride)] = cmul(v[r], w);
-            if (r + 1 < R) w = cmul(w, g);
+            row[dj + (uint32_t)A1 * (uint32_t)(r * stride)] = cmul(v[r], w[r % CH]);
+            if (r + CH < R) w[r % CH] = cmul(w[r % CH], gc);
         }
     }
 };
 
 // grid (L / T, jobs in batch): T columns b of the A-point DFTs of one job
-template <int LOGA, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGA)) k_wide1(Params p) {
-    constexpr int NT = T * max_bfly(LOGA);
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_wide1(Params p) {
+    constexpr int NT = T * max_bfly(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
     const Job J = p.jobs[p.job0 + blockIdx.y];
     const int b0 = blockIdx.x * T;
     Wide1Fill fill{&p, &J, b0, L};
     YOut<true> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b0, 0, 1 << LOGA, 1};
-    cta_fft<LOGA, T, NT, true>(smem, p.tw_tab, fill, out, min(T, L - b0));
+    cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
 }
 
 // Pruned pass 1: column b only holds the band bins k = b mod L, i.e. the
 // sub-band a in [a0, a0 + P_b) of the A-point problem (k = b + L a), so its
 // A-point DFT is itself a band tile of L1 >= P_b points over A1 = A / L1
 // columns d1 (d = d1 + A1 c1).  grid (L * tiles_per_b, jobs in batch).
-template <int LOGL1, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGL1)) k_wide1p(Params p, int L, int tiles_per_b) {
+template <int LOGL1, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL1, MAXLR)) k_wide1p(Params p, int L, int tiles_per_b) {
     constexpr int L1 = 1 << LOGL1;
-    constexpr int NT = T * max_bfly(LOGL1);
+    constexpr int NT = T * max_bfly(LOGL1, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L1;
@@ -524,7 +618,7 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL1)) k_wide1p(Params p, int L,
     __syncthreads();
     BandFill<LOGL1> fill{&p, Zs, a0, (uint32_t)L, d0};
     YOut<false> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b, d0, A, A1};
-    cta_fft<LOGL1, T, NT, false>(buf, p.tw_tab, fill, out, min(T, A1 - d0));
+    cta_fft<LOGL1, T, NT, false, MAXLR>(buf, p.tw_tab, fill, out, min(T, A1 - d0));
 }
 
 // ------------------------------------------------------------ wide pass 2
@@ -540,17 +634,24 @@ struct YFill {
     }
 };
 
-// grid (A / T, jobs in batch): T columns d of the L-point DFTs over b
-template <int LOGL, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_wide2(Params p) {
-    constexpr int NT = T * max_bfly(LOGL);
+// grid (A / (T D), jobs in batch): D tiles of T columns d of the L-point DFTs over b
+template <int LOGL, int T, int D, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_wide2(Params p) {
+    constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     __shared__ double red[2 * ((NT + 31) / 32)];
     const Job J = p.jobs[p.job0 + blockIdx.y];
-    const int d0 = blockIdx.x * T;
-    YFill fill{p.Y + (int64_t)blockIdx.y * p.M, p.A, d0};
-    WOut out = make_wout(p, J, d0);
-    cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
+    const int dbase = blockIdx.x * T * D;
+    WOut<CROP> out = make_wout<CROP>(p, J, dbase);
+#pragma unroll 1
+    for (int q = 0; q < D; q++) {
+        const int d0 = dbase + q * T;
+        if (d0 >= p.A) break;
+        if (q > 0) __syncthreads();
+        YFill fill{p.Y + (int64_t)blockIdx.y * p.M, p.A, d0};
+        out.d0 = d0;
+        cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
+    }
     write_partials<NT>(p, J, out, blockIdx.x, red);
 }
 
@@ -583,30 +684,30 @@ struct FOut {
 };
 
 // pass 1 of the forward: grid L / T, A-point DFTs of the columns b
-template <int LOGA, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGA)) k_fwd1(Params p) {
-    constexpr int NT = T * max_bfly(LOGA);
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_fwd1(Params p) {
+    constexpr int NT = T * max_bfly(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
     const int b0 = blockIdx.x * T;
     SigFill fill{&p, b0, L};
     YOut<true> out{&p, p.Y, b0, 0, 1 << LOGA, 1};
-    cta_fft<LOGA, T, NT, true>(smem, p.tw_tab, fill, out, min(T, L - b0));
+    cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
 }
 
 // pass 2 of the forward (or the whole forward when A = 1): grid A / T
-template <int LOGL, int T>
-__global__ void __launch_bounds__(T * max_bfly(LOGL)) k_fwd2(Params p) {
-    constexpr int NT = T * max_bfly(LOGL);
+template <int LOGL, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_fwd2(Params p) {
+    constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     const int d0 = blockIdx.x * T;
     FOut out{p.Fp_out, p.A, d0, p.M >> 1};
     if (p.A == 1) {
         SigFill fill{&p, 0, 1};
-        cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, 1);
+        cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, 1);
     } else {
         YFill fill{p.Y, p.A, d0};
-        cta_fft<LOGL, T, NT, false>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
+        cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
     }
 }
 
