@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <set>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -20,18 +22,18 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr int kMaxLogM = 25;           // M <= 2^25 (zero boundary of N = 2^24)
-constexpr int kBandMaxLog = 12;        // band kernels up to L = 4096 when M > kLmax
+constexpr int kBandMaxLog = 10;        // band kernels up to L = 1024 when M > kLmax
 constexpr int kWideLog = 10;           // pass-2 DFT length of wide scales (M <= 2^23)
-constexpr size_t kWideBatchBytes = size_t(64) << 20;   // intermediate per wide launch (L2-sized)
+constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide launch; one per stream
 
 // ----------------------------------------------------------- launch shapes
 
 // threads per CTA are T * max_bfly(LOGL); aim at 256 threads (128 for one-stage DFTs)
 constexpr int kThreadsTarget = 256;
-// (three-stage DFTs keep 4 columns for 32-byte output runs, 1 at L = 8192)
+// (three-stage DFTs keep 2 columns, 1 at L = 8192, so 128 registers fit)
 constexpr int band_T(int logl) {
     return n_stages(logl) == 1 ? 128
-         : n_stages(logl) == 3 ? (logl >= 13 ? 1 : 4)
+         : n_stages(logl) == 3 ? (logl >= 13 ? 1 : 2)
          : (kThreadsTarget / max_bfly(logl) < 1 ? 1 : kThreadsTarget / max_bfly(logl));
 }
 constexpr int wide1_T(int loga) { return band_T(loga); }
@@ -41,16 +43,21 @@ constexpr int wide1p_T(int logl) { return band_T(logl) > 32 ? 32 : band_T(logl);
 using KernFn = void (*)(Params);
 struct Entry { KernFn fn; int T, NT, logl; int D = 1; };
 
-// tiles of T columns per CTA for the W-writing kernels
-constexpr int kBandD = 8;
-constexpr int kWide2D = 2;
+// tiles of T columns per CTA of the W-writing kernels: as many as keep the
+// grid at >= kMinCtas CTAs, at most kMaxD
+constexpr int kMaxD = 8;
+constexpr int kMinCtas = 152 * 4;
+int pick_D(int64_t tiles_total) {
+    int64_t d = tiles_total / kMinCtas;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxD, d));
+}
 
 template <int LOGL, int T, bool CROP>
-Entry band_entry() { return {k_band<LOGL, T, kBandD, CROP>, T, T * max_bfly(LOGL), LOGL, kBandD}; }
+Entry band_entry() { return {k_band<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL, 1}; }
 template <int LOGL, int T>
 Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 template <int LOGL, int T, bool CROP>
-Entry wide2_entry() { return {k_wide2<LOGL, T, kWide2D, CROP>, T, T * max_bfly(LOGL), LOGL, kWide2D}; }
+Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL, 1}; }
 template <int LOGL, int T>
 Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
 template <int LOGL, int T>
@@ -162,11 +169,12 @@ struct cwt_plan {
     std::vector<double> w_tilde;
 
     std::vector<Job> jobs;
-    struct BandGroup { int logl; int ntiles; size_t tj_off; double bytes; };
+    struct BandGroup { int logl; int ntiles; int D; size_t tj_off; double bytes; };
     std::vector<BandGroup> groups;        // single-pass jobs by DFT length
     struct WideBatch { int job0; int count; int logl1; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
-    int wide_logl = 0, wide_loga = 0, wide_G = 0;
+    int wide_logl = 0, wide_loga = 0, wide_G = 0, wide_D = 1;
+    size_t y_stride = 0;                  // elements of Y per stream
     int fwd_small = 0;
     int crop = 0;                         // N < M: drop the padded outputs
     int64_t n_partials = 0;
@@ -373,8 +381,11 @@ cwt_status build_plan(cwt_plan* p) {
         cwt_plan::BandGroup g;
         g.logl = ll;
         const int64_t A = M >> ll;
-        const int T = tb.band[ll][0].T, D = tb.band[ll][0].D;
-        const int per_job = (int)((A + (int64_t)T * D - 1) / ((int64_t)T * D));
+        const int T = tb.band[ll][0].T;
+        const int64_t tiles_job = (A + T - 1) / T;
+        const int D = pick_D(tiles_job * (int64_t)by_logl[ll].size());
+        const int per_job = (int)((tiles_job + D - 1) / D);
+        g.D = D;
         g.ntiles = 0;
         g.tj_off = tile_job.size();
         g.bytes = 0;
@@ -392,9 +403,11 @@ cwt_status build_plan(cwt_plan* p) {
     p->n_band_jobs = (int64_t)p->jobs.size();
     if (!wide.empty()) {
         const int64_t A = M >> p->wide_logl;
-        const int T2 = tb.wide2[p->wide_logl][0].T, D2 = tb.wide2[p->wide_logl][0].D;
-        const int ntiles2 = (int)((A + (int64_t)T2 * D2 - 1) / ((int64_t)T2 * D2));
+        const int T2 = tb.wide2[p->wide_logl][0].T;
         p->wide_G = (int)std::max<int64_t>(1, (int64_t)(kWideBatchBytes / ((size_t)M * sizeof(float2))));
+        const int64_t tiles_job = (A + T2 - 1) / T2;
+        p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
+        const int ntiles2 = (int)((tiles_job + p->wide_D - 1) / p->wide_D);
         const int L = 1 << p->wide_logl;
         for (size_t i = 0; i < wide.size(); i++) {
             Job J = wide[i];
@@ -450,7 +463,9 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
     size_t ycount = 0;
     if (!small) ycount = (size_t)M;
-    if (!p->wide.empty()) ycount = std::max(ycount, (size_t)M * (size_t)std::min<int>(p->wide_G, (int)wide.size()));
+    p->y_stride = (size_t)M * (size_t)std::max(1, std::min<int>(p->wide_G, (int)wide.size()));
+    if (!p->wide.empty())
+        ycount = std::max(ycount, p->y_stride * (size_t)std::min<size_t>(p->wide.size(), cwt_plan::kSide + 1));
     if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
     return CWT_OK;
@@ -508,12 +523,28 @@ struct LaunchTimer {
     }
 };
 
+// Lets a kernel use all the shared memory the device allows beyond its static
+// part (once per kernel and device; dynamic requests above 48 KB need it).
+cwt_status opt_in_smem(cwt_plan* p, const void* fn) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({p->device, fn})) return CWT_OK;
+    cudaFuncAttributes fa{};
+    CWT_CUDA(p, cudaFuncGetAttributes(&fa, fn));
+    int optin = 0;
+    CWT_CUDA(p, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    CWT_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes));
+    done.insert({p->device, fn});
+    return CWT_OK;
+}
+
 cwt_status launch(cwt_plan* p, const Entry& e, dim3 grid, size_t smem, const Params& P, cudaStream_t s, int cls,
                   double bytes) {
     if (!e.fn) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
-    if (smem > 48 * 1024) {
-        CWT_CUDA(p, cudaFuncSetAttribute((const void*)e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
+    cwt_status st = opt_in_smem(p, (const void*)e.fn);
+    if (st != CWT_OK) return st;
     LaunchTimer lt(p, cls, bytes, s);
     e.fn<<<grid, e.NT, smem, s>>>(P);
     CWT_CUDA(p, cudaGetLastError());
@@ -558,11 +589,15 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
             return st;
     }
 
-    // 2. band scales, one launch per DFT length, on side streams forked after the
-    //    forward transform (they only read F); the wide batches below stay on the
-    //    call's stream because they share the intermediate Y
-    const bool fork = !p->groups.empty() && !p->wide.empty();
-    if (fork) {
+    // 2-3. band scales (one launch per DFT length) and wide-scale batches
+    //      (pass 1 then pass 2 through an L2-sized intermediate) are independent
+    //      once F exists: they are spread over the call's stream and side
+    //      streams forked after the forward transform; each stream has its own
+    //      intermediate Y.
+    const int nwork = (int)(p->groups.size() + p->wide.size());
+    const int nstreams = std::min(nwork, cwt_plan::kSide + 1);
+    cudaStream_t streams[cwt_plan::kSide + 1] = {s};
+    if (nstreams > 1) {
         if (!p->ev_fork) {
             CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
             for (int i = 0; i < cwt_plan::kSide; i++) {
@@ -571,29 +606,26 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
             }
         }
         CWT_CUDA(p, cudaEventRecord(p->ev_fork, s));
-        for (int i = 0; i < cwt_plan::kSide; i++) CWT_CUDA(p, cudaStreamWaitEvent(p->side[i], p->ev_fork, 0));
+        for (int i = 1; i < nstreams; i++) {
+            streams[i] = p->side[i - 1];
+            CWT_CUDA(p, cudaStreamWaitEvent(streams[i], p->ev_fork, 0));
+        }
     }
-    for (size_t gi = 0; gi < p->groups.size(); gi++) {
-        const auto& g = p->groups[gi];
-        const Entry& e = tb.band[g.logl][p->crop];
-        Params Q = P;
-        Q.A = (int32_t)(p->M >> g.logl);
-        Q.tile_job = p->d_tile_job + g.tj_off;
-        size_t smem = (size_t)(1 << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
-        cudaStream_t gs = fork ? p->side[gi % cwt_plan::kSide] : s;
-        if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
-    }
-
-    // 3. wide scales in L2-sized batches: pass 1 (A-point DFTs + twiddle) then pass 2
-    for (const auto& wb : p->wide) {
+    int next = 0;
+    // wide batches first (longest chains), round robin; band groups fill in
+    for (size_t wi = 0; wi < p->wide.size(); wi++) {
+        const auto& wb = p->wide[wi];
+        const int si = next++ % nstreams;
+        cudaStream_t ws = streams[si];
         const Entry& e2 = tb.wide2[p->wide_logl][p->crop];
         const int L = 1 << p->wide_logl;
         Params Q = P;
         Q.job0 = wb.job0;
         Q.A = (int32_t)(p->M >> p->wide_logl);
+        Q.Y = p->d_Y + (size_t)si * p->y_stride;
         if (wb.logl1 < 0) {
             const Entry& e1 = tb.wide1[p->wide_loga];
-            if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T, wb.count), stage_smem(p->wide_loga, e1.T), Q, s,
+            if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T, wb.count), stage_smem(p->wide_loga, e1.T), Q, ws,
                              CWT_KCLASS_WIDE1, wb.band_bytes)) != CWT_OK)
                 return st;
         } else {
@@ -602,24 +634,32 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
             const int tpb = (A1 + e1.T - 1) / e1.T;
             size_t smem = (size_t)(1 << wb.logl1) * sizeof(float2) + stage_smem(wb.logl1, e1.T);
             if (!e1.fn) return fail(p, CWT_ERR_INTERNAL, "missing pass-1 instantiation");
-            if (smem > 48 * 1024)
-                CWT_CUDA(p, cudaFuncSetAttribute((const void*)e1.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
-            LaunchTimer lt(p, CWT_KCLASS_WIDE1, wb.band_bytes, s);
-            e1.fn<<<dim3(L * tpb, wb.count), e1.NT, smem, s>>>(Q, L, tpb);
+            if ((st = opt_in_smem(p, (const void*)e1.fn)) != CWT_OK) return st;
+            LaunchTimer lt(p, CWT_KCLASS_WIDE1, wb.band_bytes, ws);
+            e1.fn<<<dim3(L * tpb, wb.count), e1.NT, smem, ws>>>(Q, L, tpb);
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
-        if ((st = launch(p, e2, dim3((Q.A + e2.T * e2.D - 1) / (e2.T * e2.D), wb.count), stage_smem(p->wide_logl, e2.T), Q, s,
+        Q.D = p->wide_D;
+        const int tiles2 = (Q.A + e2.T - 1) / e2.T;
+        if ((st = launch(p, e2, dim3((tiles2 + Q.D - 1) / Q.D, wb.count), stage_smem(p->wide_logl, e2.T), Q, ws,
                          CWT_KCLASS_WIDE2, wb.out_bytes)) != CWT_OK)
             return st;
     }
-
-    if (fork) {
-        for (int i = 0; i < cwt_plan::kSide; i++) {
-            CWT_CUDA(p, cudaEventRecord(p->ev_join[i], p->side[i]));
-            CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i], 0));
-        }
+    for (size_t gi = 0; gi < p->groups.size(); gi++) {
+        const auto& g = p->groups[gi];
+        const Entry& e = tb.band[g.logl][p->crop];
+        Params Q = P;
+        Q.A = (int32_t)(p->M >> g.logl);
+        Q.tile_job = p->d_tile_job + g.tj_off;
+        Q.D = g.D;
+        size_t smem = (size_t)(1 << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
+        cudaStream_t gs = streams[next++ % nstreams];
+        if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
+    }
+    for (int i = 1; i < nstreams; i++) {
+        CWT_CUDA(p, cudaEventRecord(p->ev_join[i - 1], streams[i]));
+        CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i - 1], 0));
     }
 
     // 4. power spectrum: fixed-order reduction of the per-tile partials

@@ -71,6 +71,7 @@ struct Params {
     int32_t M, h;            // M = 2^logM, two-level table split h
     int32_t A;               // number of columns d (= M / L)
     int32_t job0;            // wide launches: job = job0 + blockIdx.y
+    int32_t D;               // tiles per CTA of the W-writing kernels
     int32_t wavelet;
     int32_t sig_f64;
     int32_t do_power;
@@ -214,6 +215,10 @@ __host__ __device__ constexpr int max_bfly(int logl, int maxlr = 5) {
 }
 // odd smem row stride for T columns (bank spread for both thread mappings)
 __host__ __device__ constexpr int row_stride(int T) { return T == 1 ? 1 : ((T & 1) ? T : T + 1); }
+
+// CTAs per SM requested from the register allocator (caps registers at
+// 65536 / (NT * min_blocks), i.e. 128 per thread for NT <= 512)
+__host__ __device__ constexpr int min_blocks(int nt) { return nt >= 512 ? 1 : 512 / nt; }
 
 template <int LOGL, int S, int MAXLR = 5>
 struct Stage {
@@ -452,25 +457,30 @@ struct BandFill {
     }
 };
 
-// One CTA handles D consecutive tiles of T columns of one job: the band
-// values, the job descriptor and the power reduction are paid once per CTA.
-template <int LOGL, int T, int D, bool CROP, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_band(Params p) {
+// One CTA handles D consecutive tiles of T columns of one job (D = p.D at
+// run time): the band values, the job descriptor and the power reduction are
+// paid once per CTA.
+template <int LOGL, int T, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR)))
+    k_band(Params p) {
     constexpr int L = 1 << LOGL;
     constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L;
     __shared__ double red[2 * ((NT + 31) / 32)];
+    __shared__ Job sJ;
 
     const int tile = blockIdx.x;
-    const Job J = p.jobs[__ldg(&p.tile_job[tile])];
-    const int dbase = (tile - J.tile0) * T * D;
+    if (threadIdx.x == 0) sJ = p.jobs[__ldg(&p.tile_job[tile])];
+    __syncthreads();
+    const Job& J = sJ;
+    const int dbase = (tile - J.tile0) * T * p.D;
     for (int i = threadIdx.x; i < L; i += NT)
         Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
-    for (int q = 0; q < D; q++) {
+    for (int q = 0; q < p.D; q++) {
         const int d0 = dbase + q * T;
         if (d0 >= p.A) break;
         __syncthreads();
@@ -581,13 +591,15 @@ struct YOut {
 
 // grid (L / T, jobs in batch): T columns b of the A-point DFTs of one job
 template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_wide1(Params p) {
+__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_bfly(LOGA, MAXLR))) k_wide1(Params p) {
     constexpr int NT = T * max_bfly(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
-    const Job J = p.jobs[p.job0 + blockIdx.y];
+    __shared__ Job sJ;
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    __syncthreads();
     const int b0 = blockIdx.x * T;
-    Wide1Fill fill{&p, &J, b0, L};
+    Wide1Fill fill{&p, &sJ, b0, L};
     YOut<true> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b0, 0, 1 << LOGA, 1};
     cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
 }
@@ -597,13 +609,17 @@ __global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_wide1(Params p) {
 // A-point DFT is itself a band tile of L1 >= P_b points over A1 = A / L1
 // columns d1 (d = d1 + A1 c1).  grid (L * tiles_per_b, jobs in batch).
 template <int LOGL1, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL1, MAXLR)) k_wide1p(Params p, int L, int tiles_per_b) {
+__global__ void __launch_bounds__(T * max_bfly(LOGL1, MAXLR), min_blocks(T * max_bfly(LOGL1, MAXLR)))
+    k_wide1p(Params p, int L, int tiles_per_b) {
     constexpr int L1 = 1 << LOGL1;
     constexpr int NT = T * max_bfly(LOGL1, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L1;
-    const Job J = p.jobs[p.job0 + blockIdx.y];
+    __shared__ Job sJ;
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    __syncthreads();
+    const Job& J = sJ;
     const int b = blockIdx.x / tiles_per_b;
     const int d0 = (blockIdx.x - b * tiles_per_b) * T;
     const int A = p.M / L;
@@ -634,17 +650,22 @@ struct YFill {
     }
 };
 
-// grid (A / (T D), jobs in batch): D tiles of T columns d of the L-point DFTs over b
-template <int LOGL, int T, int D, bool CROP, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_wide2(Params p) {
+// grid (A / (T D), jobs in batch): D = p.D tiles of T columns d of the
+// L-point DFTs over b
+template <int LOGL, int T, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR)))
+    k_wide2(Params p) {
     constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     __shared__ double red[2 * ((NT + 31) / 32)];
-    const Job J = p.jobs[p.job0 + blockIdx.y];
-    const int dbase = blockIdx.x * T * D;
+    __shared__ Job sJ;
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    __syncthreads();
+    const Job& J = sJ;
+    const int dbase = blockIdx.x * T * p.D;
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
-    for (int q = 0; q < D; q++) {
+    for (int q = 0; q < p.D; q++) {
         const int d0 = dbase + q * T;
         if (d0 >= p.A) break;
         if (q > 0) __syncthreads();
@@ -685,7 +706,7 @@ struct FOut {
 
 // pass 1 of the forward: grid L / T, A-point DFTs of the columns b
 template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_fwd1(Params p) {
+__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_bfly(LOGA, MAXLR))) k_fwd1(Params p) {
     constexpr int NT = T * max_bfly(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
@@ -697,7 +718,7 @@ __global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR)) k_fwd1(Params p) {
 
 // pass 2 of the forward (or the whole forward when A = 1): grid A / T
 template <int LOGL, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR)) k_fwd2(Params p) {
+__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR))) k_fwd2(Params p) {
     constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     const int d0 = blockIdx.x * T;
