@@ -133,6 +133,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_signal(name: str, rank: int, world: int) -> np.ndarray:
+    """The workload signal of one replica: rank 0 (and single-GPU runs) use the
+    workload's own seed, other ranks an independent seed of the same recipe."""
+    if world <= 1 or rank == 0:
+        return synth.workload_signal(name)
+    w = synth.WORKLOADS[name]
+    seed = synth.BASE_SEED + 100 + rank
+    return synth.lognormal_field(w["n"], seed=seed) if "lognormal" in name else synth.multitone(w["n"], seed=seed)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank time over all ranks (a no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank processes units_per_step per step."""
+    return world * units_per_step * steps / (total_ms * 1e-3)
+
+
 def cpu_baseline(name, budget_s, steps=1, warmup=0):
     """The FP64 oracle (FFT tier) on the host cores over a bounded sample of the
     workload: the first scales of each boundary, sized to about budget_s."""
@@ -203,10 +229,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     w = synth.WORKLOADS[args.workload]
-    f = synth.workload_signal(args.workload)
-    if world > 1:
-        f = synth.lognormal_field(w["n"], seed=synth.BASE_SEED + 100 + rank) \
-            if "lognormal" in args.workload else synth.multitone(w["n"], seed=synth.BASE_SEED + 100 + rank)
+    f = rank_signal(args.workload, rank, world)
     sc = synth.workload_scales(args.workload)
     N, S = len(f), len(sc)
     plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b) for b in w["boundaries"]]
@@ -244,10 +267,7 @@ def run_ours(args):
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
 
     # per-kernel-class device time over the timed region
     cls_tot = {}
@@ -265,7 +285,7 @@ def run_ours(args):
     achieved = cls_tot[dom][2] / (cls_tot[dom][0] * 1e-3) / 1e9 if cls_tot[dom][0] > 0 else 0.0
     traffic = load_traffic(dom, args.workload)
     units_per_step = S * N * len(plans)
-    value = world * units_per_step * args.steps / (total_ms * 1e-3)
+    value = weak_scaling_value(units_per_step, args.steps, world, total_ms)
 
     # end to end through the host-buffer entry point: H2D of the signal, D2H of W and spectrum
     e2e = None
