@@ -15,6 +15,7 @@
 
 #include "../../include/cwt.h"
 #include "cwt_kernels.cuh"
+#include "cwt_tables.cuh"
 
 using namespace cwtk;
 
@@ -28,21 +29,6 @@ constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide 
 
 // ----------------------------------------------------------- launch shapes
 
-// threads per CTA are T * max_bfly(LOGL); aim at 256 threads (128 for one-stage DFTs)
-constexpr int kThreadsTarget = 256;
-// (three-stage DFTs keep 2 columns, 1 at L = 8192, so 128 registers fit)
-constexpr int band_T(int logl) {
-    return n_stages(logl) == 1 ? 128
-         : n_stages(logl) == 3 ? (logl >= 13 ? 1 : 2)
-         : (kThreadsTarget / max_bfly(logl) < 1 ? 1 : kThreadsTarget / max_bfly(logl));
-}
-constexpr int wide1_T(int loga) { return band_T(loga); }
-// pruned pass 1: at most 32 columns d1 per tile (A1 = A / L1 can be small)
-constexpr int wide1p_T(int logl) { return band_T(logl) > 32 ? 32 : band_T(logl); }
-
-using KernFn = void (*)(Params);
-struct Entry { KernFn fn; int T, NT, logl; int D = 1; };
-
 // tiles of T columns per CTA of the W-writing kernels: as many as keep the
 // grid at >= kMinCtas CTAs, at most kMaxD
 constexpr int kMaxD = 8;
@@ -52,68 +38,16 @@ int pick_D(int64_t tiles_total) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxD, d));
 }
 
-template <int LOGL, int T, bool CROP>
-Entry band_entry() { return {k_band<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL, 1}; }
-template <int LOGL, int T>
-Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
-template <int LOGL, int T, bool CROP>
-Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL, 1}; }
-template <int LOGL, int T>
-Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
-template <int LOGL, int T>
-Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
-
-using KernFnP = void (*)(Params, int, int);
-struct EntryP { KernFnP fn; int T, NT, logl; };
-template <int LOGL, int T>
-EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
-
-template <int... L>
-void fill_tables(Entry (*band)[2], Entry* wide1, Entry* fwd1, Entry* fwd_small, EntryP* wide1p,
-                 std::integer_sequence<int, L...>) {
-    ((band[L + 1][0] = band_entry<L + 1, band_T(L + 1), false>()), ...);
-    ((band[L + 1][1] = band_entry<L + 1, band_T(L + 1), true>()), ...);
-    ((wide1p[L + 1] = wide1p_entry<L + 1, wide1p_T(L + 1)>()), ...);
-    ((wide1[L + 1] = wide1_entry<L + 1, wide1_T(L + 1)>()), ...);
-    ((fwd1[L + 1] = fwd1_entry<L + 1, wide1_T(L + 1)>()), ...);
-    ((fwd_small[L + 1] = fwd2_entry<L + 1, 1>()), ...);
-}
-
-struct Tables {
-    Entry band[kLmaxLog + 1][2];     // [log2 L][crop]
-    Entry wide1[kLmaxLog + 1];
-    Entry fwd1[kLmaxLog + 1];
-    Entry fwd_small[kLmaxLog + 1];
-    Entry wide2[kLmaxLog + 1][2];    // [log2 L][crop]
-    Entry fwd2[kLmaxLog + 1];
-    EntryP wide1p[kLmaxLog + 1];
-    Tables() {
-        std::memset((void*)this, 0, sizeof(*this));
-        fill_tables(band, wide1, fwd1, fwd_small, wide1p, std::make_integer_sequence<int, kLmaxLog - 2>{});
-        wide1[12] = wide1_entry<12, wide1_T(12)>();
-        wide1[13] = wide1_entry<13, wide1_T(13)>();
-        fwd1[12] = fwd1_entry<12, wide1_T(12)>();
-        fwd1[13] = fwd1_entry<13, wide1_T(13)>();
-        band[12][0] = band_entry<12, band_T(12), false>();
-        band[12][1] = band_entry<12, band_T(12), true>();
-        band[13][0] = band_entry<13, band_T(13), false>();
-        band[13][1] = band_entry<13, band_T(13), true>();
-        fwd_small[12] = fwd2_entry<12, 1>();
-        fwd_small[13] = fwd2_entry<13, 1>();
-        wide2[10][0] = wide2_entry<10, band_T(10), false>();
-        wide2[10][1] = wide2_entry<10, band_T(10), true>();
-        wide2[11][0] = wide2_entry<11, band_T(11), false>();
-        wide2[11][1] = wide2_entry<11, band_T(11), true>();
-        wide2[12][0] = wide2_entry<12, band_T(12), false>();
-        wide2[12][1] = wide2_entry<12, band_T(12), true>();
-        fwd2[10] = fwd2_entry<10, band_T(10)>();
-        fwd2[11] = fwd2_entry<11, band_T(11)>();
-        fwd2[12] = fwd2_entry<12, band_T(12)>();
-    }
-};
-
 const Tables& tables() {
-    static Tables t;
+    static const Tables t = [] {
+        Tables x;
+        std::memset((void*)&x, 0, sizeof(x));
+        fill_band_tables(x);
+        fill_p1_tables(x);
+        fill_wide_tables(x);
+        fill_fwd_tables(x);
+        return x;
+    }();
     return t;
 }
 
@@ -169,9 +103,9 @@ struct cwt_plan {
     std::vector<double> w_tilde;
 
     std::vector<Job> jobs;
-    struct BandGroup { int logl; int ntiles; int D; size_t tj_off; double bytes; };
+    struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; };  // depth 2^rdi
     std::vector<BandGroup> groups;        // single-pass jobs by DFT length
-    struct WideBatch { int job0; int count; int logl1; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
+    struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
     int wide_logl = 0, wide_loga = 0, wide_G = 0, wide_D = 1;
     size_t y_stride = 0;                  // elements of Y per stream
@@ -353,12 +287,16 @@ cwt_status build_plan(cwt_plan* p) {
     const bool small = M <= kLmax;
     p->wide_logl = std::max(kWideLog, p->logM - kLmaxLog);
     p->wide_loga = p->logM - p->wide_logl;
-    std::vector<std::vector<Job>> by_logl(kLmaxLog + 1);
+    // band groups by (log2 L, direct depth): slots kLmaxLog + 1 and + 2 hold the
+    // L = 1024 groups of depth 2 and 4 (bands up to 2048 / 4096 bins)
+    std::vector<std::vector<Job>> by_logl(kLmaxLog + 3);
     std::vector<Job> wide;
     for (const Job& J : all) {
         int lk = std::max(1, ilog2(J.K));
         if (small) by_logl[std::min(lk, p->logM)].push_back(J);
         else if (lk <= kBandMaxLog) by_logl[lk].push_back(J);
+        else if (J.K <= (2 << kBandDepthLog)) by_logl[kLmaxLog + 1].push_back(J);
+        else if (J.K <= (4 << kBandDepthLog)) by_logl[kLmaxLog + 2].push_back(J);
         else wide.push_back(J);
     }
 
@@ -376,20 +314,22 @@ cwt_status build_plan(cwt_plan* p) {
             nparts += ntiles;
         }
     };
-    for (int ll = 1; ll <= kLmaxLog; ll++) {
-        if (by_logl[ll].empty()) continue;
+    for (int slot = 1; slot <= kLmaxLog + 2; slot++) {
+        if (by_logl[slot].empty()) continue;
+        const int ll = slot <= kLmaxLog ? slot : kBandDepthLog;
         cwt_plan::BandGroup g;
         g.logl = ll;
+        g.rdi = slot <= kLmaxLog ? 0 : slot - kLmaxLog;
         const int64_t A = M >> ll;
         const int T = tb.band[ll][0].T;
         const int64_t tiles_job = (A + T - 1) / T;
-        const int D = pick_D(tiles_job * (int64_t)by_logl[ll].size());
+        const int D = pick_D(tiles_job * (int64_t)by_logl[slot].size());
         const int per_job = (int)((tiles_job + D - 1) / D);
         g.D = D;
         g.ntiles = 0;
         g.tj_off = tile_job.size();
         g.bytes = 0;
-        for (Job J : by_logl[ll]) {
+        for (Job J : by_logl[slot]) {
             J.tile0 = g.ntiles;
             int idx = (int)p->jobs.size();
             for (int t = 0; t < per_job; t++) tile_job.push_back(idx);
@@ -412,13 +352,19 @@ cwt_status build_plan(cwt_plan* p) {
         for (size_t i = 0; i < wide.size(); i++) {
             Job J = wide[i];
             // pass 1 of column b has at most ceil(K / L) band bins: a pruned band tile of
-            // L1 = 2^ceil(log2) points unless that is most of the A-point DFT
+            // L1 = 2^ceil(log2) points over A1 = A / L1 columns d1, with the widest
+            // column-count variant that fits A1; the whole A-point DFT when L1 = A
             int l1 = std::max(1, ilog2(((int64_t)J.K + L - 1) / L));
-            // prune only when the A1 = A / L1 columns d1 fill at least one tile
-            if (l1 > kLmaxLog - 2 || l1 > p->wide_loga || (int64_t(1) << (p->wide_loga - l1)) < tb.wide1p[l1].T)
-                l1 = -1;
-            if (p->wide.empty() || p->wide.back().count >= p->wide_G || p->wide.back().logl1 != l1)
-                p->wide.push_back({(int)p->jobs.size(), 0, l1, 0.0, 0.0});
+            int var = -1;
+            if (l1 <= kLmaxLog - 2 && l1 < p->wide_loga) {
+                const int64_t A1 = int64_t(1) << (p->wide_loga - l1);
+                for (int q = 0; q < kP1Var && var < 0; q++)
+                    if (tb.wide1p[l1][q].T <= A1) var = q;
+            }
+            if (var < 0) l1 = -1;
+            if (p->wide.empty() || p->wide.back().count >= p->wide_G || p->wide.back().logl1 != l1 ||
+                p->wide.back().var != var)
+                p->wide.push_back({(int)p->jobs.size(), 0, l1, var, 0.0, 0.0});
             J.tile0 = 0;
             assign_parts(J, ntiles2);
             auto& wb = p->wide.back();
@@ -629,7 +575,7 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
                              CWT_KCLASS_WIDE1, wb.band_bytes)) != CWT_OK)
                 return st;
         } else {
-            const EntryP& e1 = tb.wide1p[wb.logl1];
+            const EntryP& e1 = tb.wide1p[wb.logl1][wb.var];
             const int A1 = Q.A >> wb.logl1;
             const int tpb = (A1 + e1.T - 1) / e1.T;
             size_t smem = (size_t)(1 << wb.logl1) * sizeof(float2) + stage_smem(wb.logl1, e1.T);
@@ -648,12 +594,12 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
     }
     for (size_t gi = 0; gi < p->groups.size(); gi++) {
         const auto& g = p->groups[gi];
-        const Entry& e = tb.band[g.logl][p->crop];
+        const Entry& e = g.rdi ? tb.band_rd[g.rdi][p->crop] : tb.band[g.logl][p->crop];
         Params Q = P;
         Q.A = (int32_t)(p->M >> g.logl);
         Q.tile_job = p->d_tile_job + g.tj_off;
         Q.D = g.D;
-        size_t smem = (size_t)(1 << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
+        size_t smem = (size_t)((1 << g.rdi) << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
         cudaStream_t gs = streams[next++ % nstreams];
         if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
     }

@@ -420,7 +420,13 @@ __device__ __forceinline__ void write_partials(const Params& p, const Job& J, co
 // rho = j + r NB0 of one thread, k_rho grows by NB0 per slot except once,
 // where it wraps by -L, so the twiddle is carried by a recurrence (at most
 // 32 steps) from one exact anchor.
-template <int LOGL>
+//
+// With direct depth RD > 1 the band may be up to RD L bins wide: residue rho
+// then collects the RD bins k_rho + i L (i < RD), and since
+// e^{-2 pi i (k + i L) d / Mp} = e^{-2 pi i k d / Mp} h^i with h =
+// e^{-2 pi i L d / Mp} a per-thread constant, the slot value is
+// w_rho * sum_i Zs[e + i L] h^i (Horner), Zs zero past the band.
+template <int LOGL, int RD = 1>
 struct BandFill {
     const Params* p;
     const float2* Zs;
@@ -436,8 +442,8 @@ struct BandFill {
         const int r_w = (L - e0 + nb - 1) / nb;          // slot index of the wrap (>= R: none)
         const uint32_t k0 = (uint32_t)(kb + e0);
         // e^{-2 pi i k_r d / Mp} over the slots as CH interleaved recurrences
-        // (chain depth R / CH): w_{r + CH} = w_r g^CH, times e^{-2 pi i (-L) d / Mp}
-        // once when the chain crosses the wrap slot r_w
+        // (chain depth R / CH): w_{r + CH} = w_r g^CH, times h^{-1} =
+        // e^{-2 pi i (-L) d / Mp} once when the chain crosses the wrap slot r_w
         constexpr int CH = R >= 8 ? 4 : 1;
         const float2 g = tw_m(*p, ((uint32_t)nb * d * mult) & mask);
         const float2 h = tw_m(*p, ((uint32_t)(-L) * d * mult) & mask);
@@ -449,9 +455,15 @@ struct BandFill {
 #pragma unroll
         for (int c = 1; c < CH; c++) gc = cmul(gc, g);
         const float2 gch = cmul(gc, h);
+        float2 hd = make_float2(1.f, 0.f);
+        if constexpr (RD > 1) hd = tw_m(*p, ((uint32_t)L * d * mult) & mask);   // e^{-2 pi i L d / Mp}
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            v[r] = cmul(Zs[(e0 + r * nb) & (L - 1)], w[r % CH]);
+            const int e = (e0 + r * nb) & (L - 1);
+            float2 z = Zs[e + (RD - 1) * L];
+#pragma unroll
+            for (int i = RD - 2; i >= 0; i--) z = cadd(cmul(z, hd), Zs[e + i * L]);
+            v[r] = cmul(z, w[r % CH]);
             if (r + CH < R) w[r % CH] = cmul(w[r % CH], (r < r_w && r + CH >= r_w) ? gch : gc);
         }
     }
@@ -460,14 +472,14 @@ struct BandFill {
 // One CTA handles D consecutive tiles of T columns of one job (D = p.D at
 // run time): the band values, the job descriptor and the power reduction are
 // paid once per CTA.
-template <int LOGL, int T, bool CROP, int MAXLR = 5>
+template <int LOGL, int T, bool CROP, int RD = 1, int MAXLR = 5>
 __global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR)))
     k_band(Params p) {
     constexpr int L = 1 << LOGL;
     constexpr int NT = T * max_bfly(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
-    float2* buf = smem + L;
+    float2* buf = smem + RD * L;
     __shared__ double red[2 * ((NT + 31) / 32)];
     __shared__ Job sJ;
 
@@ -476,7 +488,7 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_
     __syncthreads();
     const Job& J = sJ;
     const int dbase = (tile - J.tile0) * T * p.D;
-    for (int i = threadIdx.x; i < L; i += NT)
+    for (int i = threadIdx.x; i < RD * L; i += NT)
         Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
@@ -484,54 +496,9 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_
         const int d0 = dbase + q * T;
         if (d0 >= p.A) break;
         __syncthreads();
-        BandFill<LOGL> fill{&p, Zs, J.k_lo, 1u, d0};
+        BandFill<LOGL, RD> fill{&p, Zs, J.k_lo, 1u, d0};
         out.d0 = d0;
         cta_fft<LOGL, T, NT, false, MAXLR>(buf, p.tw_tab, fill, out, min(T, p.A - d0));
-    }
-    write_partials<NT>(p, J, out, tile - J.tile0, red);
-}
-
-// Single-stage band kernel (L <= 32) with D columns per thread: thread i of
-// the tile handles the columns d = d0 + i + NT q (q < D).  The first column's
-// inputs come from BandFill; each further column multiplies slot rho by the
-// per-job step sig[rho] = e^{-2 pi i k_rho NT / M} (a recurrence of at most
-// D - 1 steps per slot), so the band values and table anchors are paid once
-// per D columns.
-template <int LOGL, int NT, int D>
-__global__ void __launch_bounds__(NT) k_band1(Params p) {
-    constexpr int L = 1 << LOGL;
-    static_assert(LOGL <= 5, "single register stage");
-    __shared__ float2 Zs[L];
-    __shared__ float2 sig[L];
-    __shared__ double red[2 * ((NT + 31) / 32)];
-    const int tile = blockIdx.x;
-    const Job J = p.jobs[__ldg(&p.tile_job[tile])];
-    const int d0 = (tile - J.tile0) * NT * D;
-    const uint32_t mask = (uint32_t)(p.M - 1);
-    for (int i = threadIdx.x; i < L; i += NT) {
-        Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
-        const int krho = J.k_lo + ((i - J.k_lo) & (L - 1));   // band bin of residue rho = i
-        sig[i] = tw_m(p, ((uint32_t)krho * (uint32_t)NT) & mask);
-    }
-    __syncthreads();
-    BandFill<LOGL> fill{&p, Zs, J.k_lo, 1u, d0};
-    WOut<true> out = make_wout<true>(p, J, d0);
-    float2 x[L];
-    const int t0 = threadIdx.x;
-    if (d0 + t0 < p.A) fill(x, 0, t0, 1);
-#pragma unroll 1
-    for (int q = 0; q < D; q++) {
-        const int t = t0 + NT * q;
-        if (d0 + t >= p.A) break;
-        if (q > 0) {
-#pragma unroll
-            for (int r = 0; r < L; r++) x[r] = cmul(x[r], sig[r]);
-        }
-        float2 v[L];
-#pragma unroll
-        for (int r = 0; r < L; r++) v[r] = x[r];
-        dft<L>(v);
-        out(v, 0, t, 1);
     }
     write_partials<NT>(p, J, out, tile - J.tile0, red);
 }

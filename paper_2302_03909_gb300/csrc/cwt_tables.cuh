@@ -1,0 +1,64 @@
+// Kernel dispatch tables of the GB300 FFTCWT: launch shapes of every
+// kernel instantiation and the Tables the planner indexes.  The tables are
+// filled by several translation units (cwt_tab_*.cu) so that nvcc compiles
+// the template instantiations in parallel.
+#pragma once
+
+#include <utility>
+
+#include "cwt_kernels.cuh"
+
+namespace cwtk {
+
+// threads per CTA are T * max_bfly(LOGL); aim at 256 threads (128 for one-stage DFTs)
+constexpr int kThreadsTarget = 256;
+// (three-stage DFTs keep 2 columns, 1 at L = 8192, so 128 registers fit)
+constexpr int band_T(int logl) {
+    return n_stages(logl) == 1 ? 128
+         : n_stages(logl) == 3 ? (logl >= 13 ? 1 : 2)
+         : (kThreadsTarget / max_bfly(logl) < 1 ? 1 : kThreadsTarget / max_bfly(logl));
+}
+constexpr int wide1_T(int loga) { return band_T(loga); }
+// pruned pass 1: the band-kernel column count; smaller variants for small A1 = A / L1
+constexpr int wide1p_T(int logl) { return band_T(logl); }
+// pruned pass-1 variants: column count T = min(wide1p_T(L1), 128 >> q), q < kP1Var
+constexpr int kP1Var = 7;
+constexpr int p1var_T(int logl, int q) { return wide1p_T(logl) < (128 >> q) ? wide1p_T(logl) : (128 >> q); }
+// direct depths of the L = 1024 band kernel (bands up to RD * 1024 bins)
+constexpr int kBandDepthLog = 10;
+
+using KernFn = void (*)(Params);
+struct Entry { KernFn fn; int T, NT, logl; };
+using KernFnP = void (*)(Params, int, int);
+struct EntryP { KernFnP fn; int T, NT, logl; };
+
+template <int LOGL, int T, bool CROP, int RD = 1>
+Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T, bool CROP>
+Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+template <int LOGL, int T>
+EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+
+struct Tables {
+    Entry band[kLmaxLog + 1][2];            // [log2 L][crop]
+    Entry band_rd[3][2];                    // L = 1024 with direct depth 2^(i): [i][crop], i = 1, 2
+    Entry wide1[kLmaxLog + 1];
+    Entry fwd1[kLmaxLog + 1];
+    Entry fwd_small[kLmaxLog + 1];
+    Entry wide2[kLmaxLog + 1][2];           // [log2 L][crop]
+    Entry fwd2[kLmaxLog + 1];
+    EntryP wide1p[kLmaxLog + 1][kP1Var];    // [log2 L1][column-count variant]
+};
+
+void fill_band_tables(Tables& t);   // cwt_tab_band.cu
+void fill_p1_tables(Tables& t);     // cwt_tab_p1.cu
+void fill_wide_tables(Tables& t);   // cwt_tab_wide.cu
+void fill_fwd_tables(Tables& t);    // cwt_tab_fwd.cu
+
+}  // namespace cwtk
