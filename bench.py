@@ -226,7 +226,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library replays each plan's launches as a CUDA graph
+    # captured on it (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     w = synth.WORKLOADS[args.workload]
     f = rank_signal(args.workload, rank, world)

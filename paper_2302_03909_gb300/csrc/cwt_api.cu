@@ -141,6 +141,11 @@ struct cwt_plan {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kSide] = {};
 
+    // captured launch sequence, replayed while the call's pointers repeat
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[3] = {};
+    bool graphs_ok = true;
+
     // timing hook (cwt_plan_set_timing)
     struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
     bool timing = false;
@@ -206,6 +211,7 @@ void free_plan(cwt_plan* p) {
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials};
@@ -249,6 +255,8 @@ void scale_band(const cwt_plan* p, double wt, double u_lo, double u_hi, int64_t*
 }
 
 size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_stride(T) * sizeof(float2); }
+
+cwt_status opt_in_smem(cwt_plan* p, const void* fn);
 
 cwt_status build_plan(cwt_plan* p) {
     const Tables& tb = tables();
@@ -414,6 +422,31 @@ cwt_status build_plan(cwt_plan* p) {
         ycount = std::max(ycount, p->y_stride * (size_t)std::min<size_t>(p->wide.size(), cwt_plan::kSide + 1));
     if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
+
+    // side streams and events, and the shared-memory opt-in of every kernel the
+    // plan launches, are set up here so that no call made while capturing needs them
+    CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    for (int i = 0; i < cwt_plan::kSide; i++) {
+        CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
+        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
+    }
+    std::vector<const void*> fns;
+    if (small) fns.push_back((const void*)tb.fwd_small[p->logM].fn);
+    else {
+        fns.push_back((const void*)tb.fwd1[p->wide_loga].fn);
+        fns.push_back((const void*)tb.fwd2[p->wide_logl].fn);
+    }
+    for (const auto& g : p->groups)
+        fns.push_back((const void*)(g.rdi ? tb.band_rd[g.rdi][p->crop].fn : tb.band[g.logl][p->crop].fn));
+    for (const auto& wb : p->wide) {
+        fns.push_back(wb.logl1 < 0 ? (const void*)tb.wide1[p->wide_loga].fn
+                                   : (const void*)tb.wide1p[wb.logl1][wb.var].fn);
+        fns.push_back((const void*)tb.wide2[p->wide_logl][p->crop].fn);
+    }
+    for (const void* f : fns) {
+        if (!f) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
+        if ((st = opt_in_smem(p, f)) != CWT_OK) return st;
+    }
     return CWT_OK;
 }
 
@@ -505,7 +538,7 @@ cwt_status check_device(cwt_plan* p) {
     return CWT_OK;
 }
 
-cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
+cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     const Tables& tb = tables();
     cwt_status st;
     Params P = base_params(p);
@@ -544,13 +577,6 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
     const int nstreams = std::min(nwork, cwt_plan::kSide + 1);
     cudaStream_t streams[cwt_plan::kSide + 1] = {s};
     if (nstreams > 1) {
-        if (!p->ev_fork) {
-            CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-            for (int i = 0; i < cwt_plan::kSide; i++) {
-                CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
-                CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
-            }
-        }
         CWT_CUDA(p, cudaEventRecord(p->ev_fork, s));
         for (int i = 1; i < nstreams; i++) {
             streams[i] = p->side[i - 1];
@@ -615,6 +641,44 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
         CWT_CUDA(p, cudaGetLastError());
         lt.done();
     }
+    return CWT_OK;
+}
+
+// Runs the launch sequence as a CUDA graph captured on the call's stream and
+// replayed while (signal, W, spectrum) repeat.  Direct launches when timing is
+// on, on the legacy default stream, inside a caller's own capture, or if
+// capture is unavailable.
+cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (p->timing || !p->graphs_ok || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread ||
+        cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return run_launches(p, signal, W, spectrum, s);
+    if (p->gexec && p->gkey[0] == signal && p->gkey[1] == W && p->gkey[2] == spectrum) {
+        CWT_CUDA(p, cudaGraphLaunch(p->gexec, s));
+        return CWT_OK;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        p->graphs_ok = false;
+        return run_launches(p, signal, W, spectrum, s);
+    }
+    cwt_status st = run_launches(p, signal, W, spectrum, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    cudaGraphExec_t x = nullptr;
+    if (st == CWT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != CWT_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        p->graphs_ok = false;
+        return run_launches(p, signal, W, spectrum, s);
+    }
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = x;
+    p->gkey[0] = signal;
+    p->gkey[1] = W;
+    p->gkey[2] = spectrum;
+    CWT_CUDA(p, cudaGraphLaunch(x, s));
     return CWT_OK;
 }
 

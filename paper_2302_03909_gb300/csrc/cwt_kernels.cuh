@@ -282,7 +282,7 @@ __device__ __forceinline__ void cta_mid_stages(float2* buf, const float2* __rest
 // the last stage's R outputs X(j + r stride).  The last stage maps threads
 // j-fastest when LAST_JFAST (coalesced writes along the DFT index),
 // t-fastest otherwise.  Only columns t < tlim (<= T) are computed.
-template <int LOGL, int T, int NT, bool LAST_JFAST, int MAXLR, class Fill, class Out>
+template <int LOGL, int T, int NT, bool LAST_JFAST, int MAXLR, class Fill, class Out, bool FILL_IN_BUF = false>
 __device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ tw_tab, Fill& fill, Out& out,
                                         int tlim) {
     constexpr int NST = n_stages(LOGL, MAXLR);
@@ -294,9 +294,13 @@ __device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ 
         const int t = (last && LAST_JFAST) ? tid / S0::NB : tid % T;
         const int j = (last && LAST_JFAST) ? tid % S0::NB : tid / T;
         float2 v[S0::R];
-        if (j < S0::NB && t < tlim) {
+        const bool act = j < S0::NB && t < tlim;
+        if (act) {
             fill(v, j, t, S0::NB);
             dft<S0::R>(v);
+        }
+        if constexpr (FILL_IN_BUF && !last) __syncthreads();   // the fill read buf in place
+        if (act) {
             if constexpr (last) out(v, j, t, S0::NB);
             else stage_store<LOGL, 0, TT, MAXLR>(v, buf, j, t);
         }

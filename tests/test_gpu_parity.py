@@ -206,3 +206,31 @@ def test_lognormal_1m_morlet_64(env, boundary):
 def test_lognormal_4m_128_sampled(env, name, boundary):
     """N = 2^22, 128 scales: sampled outputs against the oracle, one by one."""
     _full_case(env, name, boundary, points=192)
+
+
+def test_graph_replay_matches_direct_launches(env):
+    """On a non-default stream the library captures each plan's launches once and
+    replays the graph while the pointers repeat; results equal direct launches."""
+    torch, cwt, _ = env
+    N = 1 << 17
+    f = synth.lognormal_field(N, seed=21)
+    sc = synth.log_scales(4.0, 1 << 15, 24)
+    for boundary in ("periodic", "zero"):
+        plan = cwt.cwt_plan_create(N, sc, "morlet", boundary)
+        sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+        W0, s0 = cwt.cwt_exec_with_power(plan, sig)                 # default stream: direct
+        torch.cuda.synchronize()
+        st = torch.cuda.Stream()
+        W1 = torch.empty_like(W0)
+        s1 = torch.empty_like(s0)
+        with torch.cuda.stream(st):
+            for _ in range(3):                                       # capture, then replays
+                cwt.cwt_exec_with_power(plan, sig, W1, s1, st)
+        torch.cuda.synchronize()
+        assert torch.equal(W0, W1) and torch.equal(s0, s1)
+        W2 = torch.empty_like(W0)                                    # new pointer: re-capture
+        with torch.cuda.stream(st):
+            cwt.cwt_exec(plan, sig, W2, st)
+        torch.cuda.synchronize()
+        assert torch.equal(W0, W2)
+        plan.close()
