@@ -56,10 +56,14 @@ typedef enum {
     CWT_WAVELET_GDW = 0,     /* Gaussian-derived ("Mexican-hat type"):
                                 psi(x) = C_N (2 - x^2) e^{-x^2/4},
                                 psi_hat(k) = 8 sqrt(pi) C_N k^2 e^{-k^2}, C_N = (18 pi)^{-1/4} */
-    CWT_WAVELET_MORLET = 1   /* psi(x) = C_N (e^{-i w0 x} - e^{-w0^2/2}) e^{-x^2/2},
+    CWT_WAVELET_MORLET = 1,  /* psi(x) = C_N (e^{-i w0 x} - e^{-w0^2/2}) e^{-x^2/2},
                                 psi_hat(k) = sqrt(2 pi) C_N (e^{-(k-w0)^2/2} - e^{-(k^2+w0^2)/2}),
                                 C_N = pi^{-1/4} (1 - 2 e^{-3 w0^2/4} + e^{-w0^2})^{-1/2};
                                 Table 2 prints w0 = 4, the default here is w0 = 6 */
+    CWT_WAVELET_CBSW = 2,    /* cubic B-spline wavelet: psi_hat(k) = 64 C_N sin^6(k/2) / k^4,
+                                C_N = sqrt(30/31) */
+    CWT_WAVELET_CWGDW = 3    /* cosine-weighted GDW: psi_hat(k) = sqrt(2 pi) C_N k (k cosh k - sinh k)
+                                e^{-k^2/2}, C_N = sqrt(8 / (1 + 5e)) / pi^{1/4} */
 } cwt_wavelet;
 
 typedef enum {
@@ -102,14 +106,14 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales,
 cwt_status cwt_plan_destroy(cwt_plan* plan);
 
 /* M, the plan's device workspace in bytes, and whether W is complex
- * (1: interleaved complex64, Morlet; 0: float32, GDW).  Any out-pointer may be NULL. */
+ * (1: interleaved complex64, Morlet; 0: float32, the real wavelets).  Any out-pointer may be NULL. */
 cwt_status cwt_plan_info(const cwt_plan* plan, int64_t* fft_len, size_t* workspace_bytes,
                          int32_t* out_is_complex);
 
 /* W = CWT of one signal (Eqs. 8-10).
  * signal_dev: N contiguous f32 (or f64 with CWT_INPUT_F64), device, >= 4 (8) B aligned.
- * W_dev: [n_scales][N] row-major, device; f32 for the GDW, interleaved complex64
- *        (re, im) for the Morlet; 4 B (GDW) or 8 B (Morlet) aligned.
+ * W_dev: [n_scales][N] row-major, device; f32 for the real wavelets (GDW, CBSW,
+ *        CW-GDW), interleaved complex64 (re, im) for the Morlet; 4 B or 8 B aligned.
  * Row s holds scale scales[s]. */
 cwt_status cwt_exec(cwt_plan* plan, const void* signal_dev, void* W_dev, void* stream);
 
@@ -125,6 +129,31 @@ cwt_status cwt_exec_with_power(cwt_plan* plan, const void* signal_dev, void* W_d
 cwt_status cwt_wavelet_power(cwt_plan* plan, const void* W_dev, double* spectrum_dev,
                              void* stream);
 
+/* Environment-dependent wavelet power spectrum (Sec. 5, Eqs. 41 and 43) with the
+ * paper's two environments, delta > 0 (overdense) and delta < 0 (underdense):
+ *   p_pos[s] = <|W(s,n)|^2> over the positions n with delta(n) > 0,
+ *   p_neg[s] = <|W(s,n)|^2> over the positions n with delta(n) < 0,
+ *   frac[0] = N_pos / N, frac[1] = N_neg / N,
+ * so that P(s) = frac[0] p_pos[s] + frac[1] p_neg[s] when no delta(n) is 0
+ * (Eq. 43).  delta_dev: N samples of the environment field (the dtype of the
+ * plan's input; usually the transformed density field itself).  All pointers
+ * are device memory; outputs are float64 (p_pos, p_neg: n_scales values; an
+ * environment with no position gets 0).  Fixed-order reductions: repeated calls
+ * give bit-identical results.  Allocates its partial sums on the first call. */
+cwt_status cwt_env_power(cwt_plan* plan, const void* W_dev, const void* delta_dev, double* p_pos_dev,
+                         double* p_neg_dev, double* frac_dev, void* stream);
+
+/* Inverse CWT over the plan's scales (Sec. 2, Eq. 6 for the real even
+ * wavelets, Eq. 5 for the Morlet):
+ *   f(n) - mean(f) ~= (1/K_psi) int_0^inf W(w, n) / sqrt(w) dw
+ * (real part doubled for the Morlet), with the integral taken by the
+ * trapezoid rule in ln w over the plan's scales (w = w~ / dx) and K_psi the
+ * wavelet's admissibility constant (Table 2; for the Morlet computed by
+ * quadrature at the plan's omega0).  The mean, which the CWT removes, is not
+ * restored.  The reconstruction is as good as the scale grid covers the
+ * signal's band.  f_out_dev: N float32, device.  Needs n_scales >= 2. */
+cwt_status cwt_icwt(cwt_plan* plan, const void* W_dev, float* f_out_dev, void* stream);
+
 /* Host-buffer form of cwt_exec_with_power: copies the signal from host memory,
  * runs the transform in plan-owned device buffers (allocated on first use) and
  * copies W and, if spectrum_host is not NULL, the spectrum back.  Pinned host
@@ -134,7 +163,8 @@ cwt_status cwt_exec_host(cwt_plan* plan, const void* signal_host, void* W_host,
 
 /* The paper's scale grid (Sec. 3.1): w~ = w~_min 2^{i + j/n_subs} with
  * w~_min = c_w pi / N and i < N_levs = Nint(log2 N), written as w~ values in
- * ascending order.  c_w = 2/sqrt(5) (GDW) or 2 / (w0 + sqrt(w0^2 + 2)) (Morlet).
+ * ascending order.  c_w = 2/sqrt(5) (GDW), 0.466094761079290 (CBSW), 0.428218886729052
+ * (CW-GDW) or 2 / (w0 + sqrt(w0^2 + 2)) (Morlet).
  * *n_out receives N_levs * n_subs; w_tilde_out may be NULL to query the count. */
 cwt_status cwt_scales_paper_grid(int64_t N, int32_t wavelet, double omega0, int32_t n_subs,
                                  double* w_tilde_out, int32_t* n_out);

@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
 of the benchmark load this module; the CUDA library never does, and this
 module imports nothing from it.  The oracle is a plain C restatement of the
-paper's definitions (Eq. 4 direct sum; Eqs. 8-10 FFTCWT; Eq. 42 power) and is
-built with gcc on first use (or by ``build()``).
+paper's definitions (Eq. 4 direct sum; Eqs. 8-10 FFTCWT; Eq. 42 power;
+Eqs. 41 and 43 environment power) and is built with gcc on first use (or by
+``build()``); the inverse CWT (Eqs. 5 and 6) and its constant K_psi are
+written here in numpy.
 
 Scales are passed as dilations ``s`` in samples and converted to the paper's
 dimensionless scale w~ = 1/s here, unless ``w_tilde=True``.
@@ -229,3 +231,42 @@ def env_power(W, delta):
                              ctypes.byref(fp), ctypes.byref(fn)) != 0:
         raise RuntimeError("orc_env_power failed")
     return pp, pn, fp.value, fn.value
+
+
+# Table 2 closed forms of K_psi = int_0^inf psi_hat(k) / k dk
+_K_CLOSED = {
+    "cbsw": lambda: 0.5 * np.sqrt(15.0 / 62.0) * (27.0 * np.log(3.0) - 32.0 * np.log(2.0)),
+    "gdw": lambda: 2.0 * (8.0 * np.pi / 9.0) ** 0.25,
+    "cwgdw": lambda: 4.0 * np.pi ** 0.25 / np.sqrt(1.0 + 5.0 * np.e),
+}
+
+
+def admissibility(wavelet: str, omega0: float = 6.0) -> float:
+    """K_psi = int_0^inf psi_hat(k)/k dk, the constant of Eqs. 5 and 6.
+    CBSW, GDW and CW-GDW: the closed forms printed in Table 2.  Morlet (any
+    omega0): adaptive quadrature of the oracle's psi_hat."""
+    if wavelet in _K_CLOSED:
+        return float(_K_CLOSED[wavelet]())
+    from scipy import integrate
+    lib = _load()
+    g = lambda k: lib.orc_psi_hat(WAVELETS[wavelet], omega0, k) / k
+    return integrate.quad(g, 0.0, omega0 + 40.0, limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+
+
+def icwt(W, scales, wavelet: str, omega0: float = 6.0, dx: float = 1.0,
+         w_tilde: bool = False) -> np.ndarray:
+    """Inverse CWT over a finite set of scales (Sec. 2): Eq. 6 for the real even
+    wavelets, Eq. 5 (twice the real part) for the Morlet, without the mean
+    term.  The discrete W of Eq. 7 equals W_f(w, x) at w = w~ / dx, and the
+    scale integral int_0^inf W / sqrt(w) dw = int W sqrt(w) d(ln w) is taken by
+    the trapezoid rule in ln w over the scales sorted by w."""
+    W = np.asarray(W)
+    w = _wt(scales, w_tilde) / dx
+    order = np.argsort(w, kind="stable")
+    lnw = np.log(w[order])
+    g = W[order] * np.sqrt(w[order])[:, None]
+    integral = np.zeros(W.shape[1], dtype=np.complex128)
+    for i in range(len(lnw) - 1):
+        integral += 0.5 * (lnw[i + 1] - lnw[i]) * (g[i] + g[i + 1])
+    rec = integral.real / admissibility(wavelet, omega0)
+    return 2.0 * rec if wavelet == "morlet" else rec

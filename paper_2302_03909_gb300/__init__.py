@@ -21,12 +21,13 @@ from . import build as _build
 
 __all__ = [
     "CwtError", "Plan", "cwt_plan_create", "cwt_plan_destroy", "cwt_plan_info", "cwt_exec",
-    "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host", "cwt_scales_paper_grid",
+    "cwt_exec_with_power", "cwt_wavelet_power", "cwt_env_power", "cwt_icwt", "cwt_exec_host",
+    "cwt_scales_paper_grid",
     "cwt_status_string", "cwt_wavelet_power_noalloc", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
     "ABI_FUNCTIONS", "KERNEL_CLASSES",
 ]
 
-WAVELETS = {"gdw": 0, "mexhat": 0, "morlet": 1}
+WAVELETS = {"gdw": 0, "mexhat": 0, "morlet": 1, "cbsw": 2, "cwgdw": 3}
 BOUNDARIES = {"periodic": 0, "zero": 1}
 SCALE_UNITS = {"dilation": 0, "w_tilde": 1}
 INPUT_DTYPES = {"f32": 0, "f64": 1}
@@ -36,7 +37,7 @@ ABI_FUNCTIONS = [
     "cwt_plan_opts_default", "cwt_plan_create", "cwt_plan_create_ex", "cwt_plan_destroy",
     "cwt_plan_info", "cwt_exec", "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host",
     "cwt_scales_paper_grid", "cwt_status_string", "cwt_plan_last_error", "cwt_plan_set_timing",
-    "cwt_plan_get_timing", "cwt_wavelet_power_noalloc",
+    "cwt_plan_get_timing", "cwt_wavelet_power_noalloc", "cwt_env_power", "cwt_icwt",
 ]
 NOALLOC_MAX_PARTIALS = 65536
 NOALLOC_CHUNK = 32768
@@ -101,6 +102,10 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.cwt_plan_get_timing.argtypes = [vp, i32, pd, ctypes.POINTER(i64), pd]
         lib.cwt_wavelet_power_noalloc.restype = ctypes.c_int
         lib.cwt_wavelet_power_noalloc.argtypes = [vp, i64, i32, i32, vp, vp]
+        lib.cwt_env_power.restype = ctypes.c_int
+        lib.cwt_env_power.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.cwt_icwt.restype = ctypes.c_int
+        lib.cwt_icwt.argtypes = [vp, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -259,6 +264,39 @@ def cwt_wavelet_power(plan: Plan, W, spectrum=None, stream=None):
     _check(load_library().cwt_wavelet_power(plan._h, _dev_ptr(W, "W"), _dev_ptr(spectrum, "spectrum"),
                                             _stream_ptr(stream)), plan)
     return spectrum
+
+
+def cwt_env_power(plan: Plan, W, delta, stream=None):
+    """Eqs. 41 and 43: (p_pos, p_neg, frac) -- the power spectrum of W over the
+    positions with delta > 0 and with delta < 0, and the two environments'
+    fractions of the N positions.  delta: N values on the device, in the plan's
+    input dtype."""
+    import torch
+    _check_W(plan, W)
+    want = torch.float64 if plan.opts["input_dtype"] == "f64" else torch.float32
+    if delta.dtype != want or delta.numel() != plan.N or not delta.is_contiguous():
+        raise ValueError(f"delta must be {plan.N} contiguous {want} values")
+    p_pos = torch.empty(plan.n_scales, dtype=torch.float64, device=W.device)
+    p_neg = torch.empty_like(p_pos)
+    frac = torch.empty(2, dtype=torch.float64, device=W.device)
+    _check(load_library().cwt_env_power(plan._h, _dev_ptr(W, "W"), _dev_ptr(delta, "delta"),
+                                        _dev_ptr(p_pos, "p_pos"), _dev_ptr(p_neg, "p_neg"),
+                                        _dev_ptr(frac, "frac"), _stream_ptr(stream)), plan)
+    return p_pos, p_neg, frac
+
+
+def cwt_icwt(plan: Plan, W, out=None, stream=None):
+    """Inverse CWT over the plan's scales (Eq. 6; Eq. 5 for the Morlet): the
+    signal minus its mean, as N float32 values on the device."""
+    import torch
+    _check_W(plan, W)
+    if out is None:
+        out = torch.empty(plan.N, dtype=torch.float32, device=W.device)
+    elif out.dtype != torch.float32 or out.numel() != plan.N or not out.is_contiguous():
+        raise ValueError(f"out must be {plan.N} contiguous float32 values")
+    _check(load_library().cwt_icwt(plan._h, _dev_ptr(W, "W"), _dev_ptr(out, "out"),
+                                   _stream_ptr(stream)), plan)
+    return out
 
 
 def cwt_exec_host(plan: Plan, signal, W, spectrum=None, stream=None):

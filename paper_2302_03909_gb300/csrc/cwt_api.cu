@@ -16,6 +16,7 @@
 #include "../../include/cwt.h"
 #include "cwt_kernels.cuh"
 #include "cwt_tables.cuh"
+#include "cwt_plan_impl.h"
 
 using namespace cwtk;
 
@@ -57,11 +58,20 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 // FP64 wavelet spectra of Table 2 for planning, up to the constant factor
 double psi_hat_shape(int wavelet, double omega0, double u) {
     if (wavelet == CWT_WAVELET_GDW) return u * u * std::exp(-u * u);
+    if (wavelet == CWT_WAVELET_CBSW) {
+        if (u == 0.0) return 0.0;
+        double sn = std::sin(0.5 * u), s2 = sn * sn;
+        return s2 * s2 * s2 / (u * u * u * u);
+    }
+    if (wavelet == CWT_WAVELET_CWGDW)
+        return u * 0.5 * ((u - 1.0) * std::exp(u - 0.5 * u * u) + (u + 1.0) * std::exp(-u - 0.5 * u * u));
     return std::exp(-0.5 * (u - omega0) * (u - omega0)) - std::exp(-0.5 * (u * u + omega0 * omega0));
 }
 
 double wavelet_cn(int wavelet, double omega0) {
     if (wavelet == CWT_WAVELET_GDW) return std::pow(18.0 * kPi, -0.25);
+    if (wavelet == CWT_WAVELET_CBSW) return std::sqrt(30.0 / 31.0);
+    if (wavelet == CWT_WAVELET_CWGDW) return std::sqrt(8.0 / (1.0 + 5.0 * std::exp(1.0))) / std::pow(kPi, 0.25);
     double w2 = omega0 * omega0;
     return std::pow(kPi, -0.25) / std::sqrt(1.0 - 2.0 * std::exp(-0.75 * w2) + std::exp(-w2));
 }
@@ -69,12 +79,16 @@ double wavelet_cn(int wavelet, double omega0) {
 // psi_hat(u) = C * shape(u): C = 8 sqrt(pi) C_N (GDW), sqrt(2 pi) C_N (Morlet)
 double wavelet_spectrum_const(int wavelet, double omega0) {
     double cn = wavelet_cn(wavelet, omega0);
-    return wavelet == CWT_WAVELET_GDW ? 8.0 * std::sqrt(kPi) * cn : std::sqrt(2.0 * kPi) * cn;
+    if (wavelet == CWT_WAVELET_GDW) return 8.0 * std::sqrt(kPi) * cn;
+    if (wavelet == CWT_WAVELET_CBSW) return 64.0 * cn;
+    return std::sqrt(2.0 * kPi) * cn;   // Morlet, CW-GDW
 }
 
 // [u_lo, u_hi] outside which |psi_hat| < eps * max |psi_hat|
 void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* u_hi) {
-    const double step = 1.0 / 1024.0, U = 80.0;
+    // the CBSW spectrum only decays as u^-4: scan further, more coarsely
+    const bool slow = wavelet == CWT_WAVELET_CBSW;
+    const double step = slow ? 1.0 / 64.0 : 1.0 / 1024.0, U = slow ? 8192.0 : 80.0;
     double mx = 0.0;
     for (double u = -U; u <= U; u += step) mx = std::max(mx, std::fabs(psi_hat_shape(wavelet, omega0, u)));
     double lo = U, hi = -U;
@@ -93,71 +107,6 @@ void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* 
 
 // ====================================================================== plan
 
-struct cwt_plan {
-    int64_t N = 0, M = 0;
-    int logM = 0, h = 0;
-    int32_t S = 0;
-    int wavelet = 0, boundary = 0;
-    cwt_plan_opts opts{};
-    int device = -1;
-    std::vector<double> w_tilde;
-
-    std::vector<Job> jobs;
-    struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; };  // depth 2^rdi
-    std::vector<BandGroup> groups;        // single-pass jobs by DFT length
-    struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
-    std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
-    int wide_logl = 0, wide_loga = 0, wide_G = 0, wide_D = 1;
-    size_t y_stride = 0;                  // elements of Y per stream
-    int fwd_small = 0;
-    int crop = 0;                         // N < M: drop the padded outputs
-    int64_t n_partials = 0;
-    std::vector<int32_t> part_off, part_cnt;
-    int64_t n_band_jobs = 0;
-
-    // device memory
-    Job* d_jobs = nullptr;
-    int32_t* d_tile_job = nullptr;
-    int32_t* d_part_off = nullptr;
-    int32_t* d_part_cnt = nullptr;
-    float2* d_Fp = nullptr;
-    float2* d_Y = nullptr;
-    double* d_partials = nullptr;
-    float2* d_tw_lo = nullptr;
-    float2* d_tw_hi = nullptr;
-    float2* d_tw_tab = nullptr;
-    size_t ws_bytes = 0;
-    // cwt_exec_host buffers
-    void* h_sig = nullptr;
-    void* h_W = nullptr;
-    double* h_spec = nullptr;
-    // cwt_wavelet_power scratch
-    double* d_pw_partials = nullptr;
-    int64_t pw_chunks = 0;
-
-    // band groups run on side streams forked from the call's stream
-    static constexpr int kSide = 2;
-    cudaStream_t side[kSide] = {};
-    cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[kSide] = {};
-
-    // captured launch sequence, replayed while the call's pointers repeat
-    cudaGraphExec_t gexec = nullptr;
-    const void* gkey[3] = {};
-    bool graphs_ok = true;
-
-    // timing hook (cwt_plan_set_timing)
-    struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<TimedLaunch> pending;
-    double t_ms[CWT_KCLASS_COUNT] = {};
-    int64_t t_launches[CWT_KCLASS_COUNT] = {};
-    double t_bytes[CWT_KCLASS_COUNT] = {};
-    double fwd_in_bytes = 0, fwd_out_bytes = 0;
-
-    std::string err;
-};
 
 namespace {
 
@@ -214,7 +163,7 @@ void free_plan(cwt_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
-                    p->h_spec, p->d_pw_partials};
+                    p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -266,7 +215,7 @@ cwt_status build_plan(cwt_plan* p) {
     if (!full) wavelet_band(p->wavelet, p->opts.omega0, p->opts.eps_trunc, &u_lo, &u_hi);
 
     // jobs: GDW pairs (2i, 2i+1); Morlet one scale each
-    const int per = (p->wavelet == CWT_WAVELET_GDW) ? 2 : 1;
+    const int per = wav_real(p->wavelet) ? 2 : 1;
     std::vector<Job> all;
     for (int s0 = 0; s0 < p->S; s0 += per) {
         Job J{};
@@ -686,7 +635,8 @@ bool aligned(const void* q, size_t a) { return ((uintptr_t)q % a) == 0; }
 
 }  // namespace
 
-// ====================================================================== ABI
+cwt_status plan_fail(cwt_plan* p, cwt_status st, const char* msg) { return fail(p, st, msg); }
+cwt_status plan_check_device(cwt_plan* p) { return check_device(p); }
 
 // ====================================================================== ABI
 
@@ -717,7 +667,7 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     cwt_plan_opts_default(&o);
     if (opts) o = *opts;
     if (N < 2 || n_scales < 1 || !scales) return CWT_ERR_INVALID_ARG;
-    if (wavelet != CWT_WAVELET_GDW && wavelet != CWT_WAVELET_MORLET) return CWT_ERR_INVALID_ARG;
+    if (wavelet < CWT_WAVELET_GDW || wavelet > CWT_WAVELET_CWGDW) return CWT_ERR_INVALID_ARG;
     if (boundary != CWT_BOUNDARY_PERIODIC && boundary != CWT_BOUNDARY_ZERO) return CWT_ERR_INVALID_ARG;
     if (o.scale_unit != CWT_SCALE_DILATION && o.scale_unit != CWT_SCALE_W_TILDE) return CWT_ERR_INVALID_ARG;
     if (o.input_dtype != CWT_INPUT_F32 && o.input_dtype != CWT_INPUT_F64) return CWT_ERR_INVALID_ARG;
@@ -865,6 +815,8 @@ cwt_status cwt_scales_paper_grid(int64_t N, int32_t wavelet, double omega0, int3
     if (N < 2 || n_subs < 1 || !n_out) return CWT_ERR_INVALID_ARG;
     double cw;
     if (wavelet == CWT_WAVELET_GDW) cw = 2.0 / std::sqrt(5.0);
+    else if (wavelet == CWT_WAVELET_CBSW) cw = 0.466094761079290;     // Table 2, footnote b
+    else if (wavelet == CWT_WAVELET_CWGDW) cw = 0.428218886729052;    // Table 2, footnote c
     else if (wavelet == CWT_WAVELET_MORLET) {
         if (!(omega0 > 0.0)) return CWT_ERR_INVALID_ARG;
         cw = 2.0 / (omega0 + std::sqrt(omega0 * omega0 + 2.0));

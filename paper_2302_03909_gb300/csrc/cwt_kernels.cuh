@@ -33,7 +33,10 @@ namespace cwtk {
 constexpr int kLmaxLog = 13;              // largest DFT held by one CTA
 constexpr int kLmax = 1 << kLmaxLog;
 
-enum { WAV_GDW = 0, WAV_MORLET = 1 };
+enum { WAV_GDW = 0, WAV_MORLET = 1, WAV_CBSW = 2, WAV_CWGDW = 3 };   // Table 2
+
+// real, even wavelets give real rows; two scales share one complex transform
+__host__ __device__ constexpr bool wav_real(int w) { return w != WAV_MORLET; }
 
 // Per-scale generator of amp * psi_hat(alpha k) in FP32 from FP64-derived constants.
 struct ScaleGen {
@@ -101,6 +104,15 @@ __device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float h
         float v2 = v * v;
         return g.amp * v2 * expf(-v2);
     }
+    if (wavelet == WAV_CBSW) {                              // 64 C_N sin^6(u/2) / u^4
+        if (v == 0.f) return 0.f;
+        const float sn = sinf(0.5f * v), s2 = sn * sn, v2 = v * v;
+        return g.amp * (s2 * s2 * s2) / (v2 * v2);
+    }
+    if (wavelet == WAV_CWGDW) {                             // sqrt(2 pi) C_N u (u cosh u - sinh u) e^{-u^2/2}
+        const float h = -0.5f * v * v;
+        return g.amp * v * 0.5f * ((v - 1.f) * expf(v + h) + (v + 1.f) * expf(h - v));
+    }
     float d = (float)(k - g.k0_int) - g.k0_frac;           // k - omega0/alpha, exact integer part
     float t = fmaf(g.a_hi, d, g.a_lo * d);                 // alpha k - omega0
     return g.amp * (expf(-0.5f * t * t) - expf(fmaf(-0.5f * v, v, -half_w0sq)));
@@ -116,7 +128,7 @@ __device__ __forceinline__ float2 spec_at(const float2* __restrict__ Fp, int k) 
 __device__ __forceinline__ float2 band_value(const Params& p, const Job& J, int k) {
     float2 f = spec_at(p.Fp, k);
     float g0 = psi_gen(J.g[0], p.wavelet, p.half_w0sq, k);
-    if (p.wavelet == WAV_GDW) {
+    if (wav_real(p.wavelet)) {
         float g1 = J.g[1].row >= 0 ? psi_gen(J.g[1], p.wavelet, p.half_w0sq, k) : 0.f;
         return make_float2(fmaf(f.x, g0, -f.y * g1), fmaf(f.x, g1, f.y * g0));
     }
@@ -393,7 +405,7 @@ __device__ __forceinline__ WOut<CROP> make_wout(const Params& p, const Job& J, i
     o.p = &p;
     o.d0 = d0;
     o.pw0 = o.pw1 = 0.f;
-    if (p.wavelet == WAV_GDW) {
+    if (wav_real(p.wavelet)) {
         o.rc = nullptr;
         o.r0 = (float*)p.W + (int64_t)J.g[0].row * p.N;
         o.r1 = J.g[1].row >= 0 ? (float*)p.W + (int64_t)J.g[1].row * p.N : nullptr;
@@ -411,7 +423,7 @@ __device__ __forceinline__ void write_partials(const Params& p, const Job& J, co
     block_sum2<NT>(o.pw0, o.pw1, &s0, &s1, red);
     if (threadIdx.x == 0) {
         p.partials[J.g[0].part_off + slot] = s0;
-        if (J.g[1].row >= 0 && p.wavelet == WAV_GDW) p.partials[J.g[1].part_off + slot] = s1;
+        if (J.g[1].row >= 0 && wav_real(p.wavelet)) p.partials[J.g[1].part_off + slot] = s1;
     }
 }
 

@@ -1,0 +1,87 @@
+// Internal: the plan object shared by the translation units of the library
+// (planner and launches in cwt_api.cu, statistics of W in cwt_stats.cu).
+// Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cwt.h"
+#include "cwt_kernels.cuh"
+
+struct cwt_plan {
+    int64_t N = 0, M = 0;
+    int logM = 0, h = 0;
+    int32_t S = 0;
+    int wavelet = 0, boundary = 0;
+    cwt_plan_opts opts{};
+    int device = -1;
+    std::vector<double> w_tilde;
+
+    std::vector<cwtk::Job> jobs;
+    struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; };  // depth 2^rdi
+    std::vector<BandGroup> groups;        // single-pass jobs by DFT length
+    struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
+    std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
+    int wide_logl = 0, wide_loga = 0, wide_G = 0, wide_D = 1;
+    size_t y_stride = 0;                  // elements of Y per stream
+    int fwd_small = 0;
+    int crop = 0;                         // N < M: drop the padded outputs
+    int64_t n_partials = 0;
+    std::vector<int32_t> part_off, part_cnt;
+    int64_t n_band_jobs = 0;
+
+    // device memory
+    cwtk::Job* d_jobs = nullptr;
+    int32_t* d_tile_job = nullptr;
+    int32_t* d_part_off = nullptr;
+    int32_t* d_part_cnt = nullptr;
+    float2* d_Fp = nullptr;
+    float2* d_Y = nullptr;
+    double* d_partials = nullptr;
+    float2* d_tw_lo = nullptr;
+    float2* d_tw_hi = nullptr;
+    float2* d_tw_tab = nullptr;
+    size_t ws_bytes = 0;
+    // cwt_exec_host buffers
+    void* h_sig = nullptr;
+    void* h_W = nullptr;
+    double* h_spec = nullptr;
+    // cwt_wavelet_power scratch
+    double* d_pw_partials = nullptr;
+    int64_t pw_chunks = 0;
+    // cwt_env_power and cwt_icwt scratch (allocated on first use)
+    double* d_env_part = nullptr;
+    int64_t* d_env_cnt = nullptr;
+    double* d_icwt_coef = nullptr;
+
+    // band groups run on side streams forked from the call's stream
+    static constexpr int kSide = 2;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kSide] = {};
+
+    // captured launch sequence, replayed while the call's pointers repeat
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[3] = {};
+    bool graphs_ok = true;
+
+    // timing hook (cwt_plan_set_timing)
+    struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<TimedLaunch> pending;
+    double t_ms[CWT_KCLASS_COUNT] = {};
+    int64_t t_launches[CWT_KCLASS_COUNT] = {};
+    double t_bytes[CWT_KCLASS_COUNT] = {};
+    double fwd_in_bytes = 0, fwd_out_bytes = 0;
+
+    std::string err;
+};
+
+// records msg as the plan's last error and returns st
+cwt_status plan_fail(cwt_plan* p, cwt_status st, const char* msg);
+// CWT_ERR_INVALID_ARG unless the current device is the plan's
+cwt_status plan_check_device(cwt_plan* p);

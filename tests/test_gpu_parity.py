@@ -90,6 +90,13 @@ CASES = [
     (1 << 17, "periodic", "gdw", 2.0, 1 << 15, 7, {"eps_trunc": 0.0}),
     (3000, "zero", "morlet", 5.0, 600.0, 6, {"fft_len": 1 << 14}),
     (1 << 12, "periodic", "morlet", 4.0, 1000.0, 6, {"omega0": 4.0, "dx": 0.25}),
+    # the other two real wavelets of Table 2 (paired like the GDW)
+    (4096, "periodic", "cbsw", 1.0, 2048.0, 12, {}),
+    (3000, "zero", "cbsw", 2.0, 1500.0, 9, {}),
+    ((1 << 16) + 5, "zero", "cbsw", 2.0, 1 << 14, 8, {}),
+    (1 << 17, "periodic", "cwgdw", 2.0, 1 << 15, 11, {}),
+    (1000, "zero", "cwgdw", 1.5, 900.0, 7, {}),
+    (1 << 14, "periodic", "cwgdw", 0.7, 4096.0, 10, {"dx": 2.0}),
 ]
 
 

@@ -259,24 +259,41 @@ def test_env_power_recovers_global(orc):
     assert np.allclose(fp * pp + fn * pn, orc.wavelet_power(W), rtol=1e-13)
 
 
-def _k_psi(orc, w, omega0):
-    return integrate.quad(lambda k: orc.psi_hat(w, k, omega0)[0] / k, 0.0, 60.0, limit=400,
-                          epsabs=1e-15, epsrel=1e-13)[0]
+ICWT_TOL = {"cbsw": 1e-7, "gdw": 1e-8, "cwgdw": 1e-12}
 
 
-@pytest.mark.parametrize("w,omega0", [("gdw", 4.0), ("morlet", 6.0)])
+@pytest.mark.parametrize("w,omega0", [("cbsw", 6.0), ("gdw", 6.0), ("cwgdw", 6.0),
+                                      ("morlet", 4.0), ("morlet", 6.0)])
 def test_inverse_cwt_reconstructs(orc, w, omega0):
-    """Eq. 6 (real even wavelet) and Eq. 5 (Morlet): the signal minus its mean is
-    (1/K_psi) int_0^inf W / sqrt(w) dw (real part doubled for the Morlet).
+    """Eq. 6 (real even wavelets) and Eq. 5 (Morlet): oracle.icwt of the oracle's
+    W over a fine log grid of scales gives back the signal minus its mean.
     Odd N: an even-length real signal's Nyquist bin is its own mirror image, so
-    the analytic-wavelet formula (Eq. 5) would count it twice."""
+    the analytic-wavelet formula (Eq. 5) would count it twice.  The Morlet's
+    floor is its psi_hat at k < 0 (about e^{-omega0^2/2}), which Eq. 5 assumes
+    zero."""
     N = 1023
     f = synth.multitone(N, periods=(16.0, 128.0, 341.0), seed=2)
-    h = 0.04
+    wt = np.exp(np.arange(math.log(2e-4), math.log(3e4), 0.04))
+    W = orc.cwt_fft(f, wt, w, omega0=omega0, w_tilde=True)
+    rec = orc.icwt(W, wt, w, omega0=omega0, w_tilde=True)
+    tol = ICWT_TOL[w] if w != "morlet" else 10.0 * math.exp(-0.5 * omega0 ** 2)
+    assert rel_l2(rec, f - f.mean()) < tol
+
+
+def test_inverse_cwt_irregular_grid_and_dx(orc):
+    """Scales in any order, unevenly spaced in ln w, and dx != 1: the trapezoid
+    rule over the sorted grid still reconstructs the signal (GDW, Eq. 6), to the
+    second-order accuracy of the trapezoid rule on an uneven grid."""
+    N = 1023
+    f = synth.multitone(N, periods=(16.0, 128.0, 341.0), seed=4)
+    rng = np.random.default_rng(7)
+    h = 0.03
     lw = np.arange(math.log(2e-4), math.log(3e4), h)
-    wt = np.exp(lw)
-    W = orc.cwt_fft(f, wt, w, omega0=omega0, w_tilde=True)       # dx = 1, w = w~
-    integral = np.sum(W / np.sqrt(wt)[:, None] * wt[:, None], axis=0) * h   # dw = w dln w
-    K = _k_psi(orc, w, omega0)
-    rec = (integral / K).real if w == "gdw" else 2.0 * (integral / K).real
-    assert rel_l2(rec, f - f.mean()) < 1e-6
+    lw += rng.uniform(-0.4, 0.4, len(lw)) * h                     # uneven gaps in (0.2h, 1.8h)
+    wt = np.exp(lw)[rng.permutation(len(lw))]
+    W = orc.cwt_fft(f, wt, "gdw", dx=0.5, w_tilde=True)
+    rec = orc.icwt(W, wt, "gdw", dx=0.5, w_tilde=True)
+    assert rel_l2(rec, f - f.mean()) < 2e-5      # second-order trapezoid on an uneven grid
+    # dilations (w~ = 1 / s) give the same numbers as the equivalent w~ grid
+    rec2 = orc.icwt(W, 1.0 / wt, "gdw", dx=0.5)
+    assert np.allclose(rec2, rec, rtol=0, atol=1e-13 * np.abs(rec).max())

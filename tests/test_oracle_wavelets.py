@@ -95,6 +95,18 @@ def test_admissibility_constant_matches_table2(orc, w):
 
 
 @pytest.mark.parametrize("w", WAVELETS)
+def test_oracle_admissibility(orc, w):
+    """oracle.admissibility (used by the inverse CWT) against the numbers printed in
+    Table 2 at omega0 = 4 and, for the Morlet, quadrature at other omega0."""
+    assert orc.admissibility(w, 4.0) == pytest.approx(table2()[w]["K"], rel=1e-12)
+    if w == "morlet":
+        for om in (3.0, 6.0, 9.0):
+            q = integrate.quad(lambda k: orc.psi_hat(w, k, om)[0] / k, 0.0, om + 60.0, limit=400,
+                               epsabs=1e-15, epsrel=1e-13)[0]
+            assert orc.admissibility(w, om) == pytest.approx(q, rel=1e-11)
+
+
+@pytest.mark.parametrize("w", WAVELETS)
 def test_cw_matches_table2(orc, w):
     # c_w = w / k_pseu: the scale at which the response to a unit-wavenumber tone,
     # proportional to |psi_hat(k/w)| / sqrt(w), peaks; i.e. 1 / argmax_u sqrt(u) |psi_hat(u)|.
