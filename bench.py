@@ -45,7 +45,30 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    # narrower cases of a workload for profiler captures (not a bench line)
+    ap.add_argument("--boundary", default="both", choices=["both", "periodic", "zero"],
+                    help="run one boundary of the workload only")
+    ap.add_argument("--scale-range", type=int, nargs=2, metavar=("I", "J"),
+                    help="keep the workload's scales I..J-1 only (ascending dilation)")
     return ap.parse_args()
+
+
+def workload_subset(args):
+    """(boundaries, scales) of the workload after --boundary / --scale-range,
+    and a description of the subset (None for the whole workload)."""
+    w = synth.WORKLOADS[args.workload]
+    bounds = tuple(w["boundaries"]) if args.boundary == "both" else (args.boundary,)
+    sc = synth.workload_scales(args.workload)
+    note = []
+    if args.boundary != "both":
+        note.append(f"{args.boundary} boundary only")
+    if args.scale_range:
+        i, j = args.scale_range
+        sc = sc[i:j]
+        note.append(f"scales {i}..{j - 1} of {w['n_scales']}")
+    if not len(sc) or not bounds:
+        raise SystemExit("empty workload subset")
+    return bounds, sc, ("; ".join(note) if note else None)
 
 
 def dist_env():
@@ -233,9 +256,9 @@ def run_ours(args):
 
     w = synth.WORKLOADS[args.workload]
     f = rank_signal(args.workload, rank, world)
-    sc = synth.workload_scales(args.workload)
+    bounds, sc, subset = workload_subset(args)
     N, S = len(f), len(sc)
-    plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b) for b in w["boundaries"]]
+    plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b) for b in bounds]
     sig = torch.tensor(f, dtype=torch.float32, device=dev)
     outs = [(p.empty_output(dev), torch.empty(S, dtype=torch.float64, device=dev)) for p in plans]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -286,7 +309,7 @@ def run_ours(args):
     dom = max(cls_tot, key=lambda k: cls_tot[k][0])
     peak, peak_src = load_peaks()
     achieved = cls_tot[dom][2] / (cls_tot[dom][0] * 1e-3) / 1e9 if cls_tot[dom][0] > 0 else 0.0
-    traffic = load_traffic(dom, args.workload)
+    traffic = load_traffic(dom, args.workload) if not subset else None
     units_per_step = S * N * len(plans)
     value = weak_scaling_value(units_per_step, args.steps, world, total_ms)
 
@@ -323,10 +346,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "n_scales": S, "wavelet": w["wavelet"],
-                       "omega0": 6.0, "boundaries": list(w["boundaries"]),
+                       "omega0": 6.0, "boundaries": list(bounds),
                        "fft_len": [p.M for p in plans], "power_spectrum": True,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
-                       "inputs": "resident in HBM", "parallelism": f"replicas x{world}"},
+                       "inputs": "resident in HBM", "parallelism": f"replicas x{world}",
+                       **({"subset": subset} if subset else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                          "peak_source": peak_src,

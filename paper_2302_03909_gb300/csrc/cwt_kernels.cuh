@@ -358,6 +358,23 @@ __device__ __forceinline__ void block_sum2(float a, float b, double* out_a, doub
 // Stores X(d + A c) for the last stage's outputs c = j + r * cstride
 // (d = d0 + t); with CROP, outputs n >= N (zero-boundary padding) are
 // dropped.  Accumulates |W|^2 per row.
+// Cache policy of the two large streams.  W is written once and never read
+// back here: its stores are cache-streaming (evict-first).  The wide-scale
+// intermediate Y is stored with an L2 evict-last policy by pass 1, so that it
+// is still on chip when pass 2 reads it, exactly once (evict-first).
+__device__ __forceinline__ void st_stream(float2* q, float2 v) { __stcs(q, v); }
+__device__ __forceinline__ void st_stream(float* q, float v) { __stcs(q, v); }
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float2* q, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(q), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float2 ld_once(const float2* q) { return __ldcs(q); }
+
 template <bool CROP>
 struct WOut {
     const Params* p;
@@ -376,7 +393,7 @@ struct WOut {
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 if (!CROP || n0 + r * step < N) {
-                    q[r * step] = v[r];
+                    st_stream(q + r * step, v[r]);
                     pw0 = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, pw0));
                 }
             }
@@ -387,10 +404,10 @@ struct WOut {
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 if (!CROP || n0 + r * step < N) {
-                    q0[r * step] = v[r].x;
+                    st_stream(q0 + r * step, v[r].x);
                     pw0 = fmaf(v[r].x, v[r].x, pw0);
                     if (two) {
-                        q1[r * step] = v[r].y;
+                        st_stream(q1 + r * step, v[r].y);
                         pw1 = fmaf(v[r].y, v[r].y, pw1);
                     }
                 }
@@ -554,6 +571,7 @@ struct YOut {
         const uint32_t d1 = (uint32_t)(COLS_B ? 0 : d0 + t);
         const uint32_t mask = (uint32_t)(p->M - 1);
         float2* row = Y + (int64_t)b * A;
+        const uint64_t pol = l2_policy_keep();
         const uint32_t dj = d1 + (uint32_t)A1 * (uint32_t)j;
         constexpr int CH = R >= 8 ? 4 : 1;                 // interleaved recurrences
         const float2 g = tw_m(*p, (b * (uint32_t)A1 * (uint32_t)stride) & mask);
@@ -566,7 +584,7 @@ struct YOut {
         for (int c = 1; c < CH; c++) gc = cmul(gc, g);
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            row[dj + (uint32_t)A1 * (uint32_t)(r * stride)] = cmul(v[r], w[r % CH]);
+            st_keep(row + (dj + (uint32_t)A1 * (uint32_t)(r * stride)), cmul(v[r], w[r % CH]), pol);
             if (r + CH < R) w[r % CH] = cmul(w[r % CH], gc);
         }
     }
@@ -629,7 +647,7 @@ struct YFill {
     template <int R>
     __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
 #pragma unroll
-        for (int r = 0; r < R; r++) v[r] = Y[(int64_t)(j + r * stride) * A + d0 + t];
+        for (int r = 0; r < R; r++) v[r] = ld_once(&Y[(int64_t)(j + r * stride) * A + d0 + t]);
     }
 };
 
