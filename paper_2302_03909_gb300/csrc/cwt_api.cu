@@ -105,6 +105,35 @@ void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* 
 
 }  // namespace
 
+// The spectrum over all M unsigned bins k = b + L a (F(k) for k <= M/2, conj
+// F(M - k) above: real signal), transposed to Ft[b A + a] so that the wide
+// scales' pass 1 reads each column b contiguously.  32 x 32 tiles through
+// shared memory; grid (ceil(L / 32), ceil(A / 32)), block (32, 8).
+static __global__ void k_spec_transpose(const float2* __restrict__ Fp, float2* __restrict__ Ft, int M, int L, int A) {
+    __shared__ float2 tile[32][33];
+    const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        const int a = a0 + i, b = b0 + tx;
+        if (a < A && b < L) {
+            const int k = b + L * a;
+            float2 f;
+            if (k <= (M >> 1)) {
+                f = __ldg(&Fp[k]);
+            } else {
+                f = __ldg(&Fp[M - k]);
+                f.y = -f.y;
+            }
+            tile[i][tx] = f;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int b = b0 + i, a = a0 + tx;
+        if (a < A && b < L) Ft[(int64_t)b * A + a] = tile[tx][i];
+    }
+}
+
 // ====================================================================== plan
 
 
@@ -161,7 +190,7 @@ void free_plan(cwt_plan* p) {
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Y,
+    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
@@ -364,6 +393,7 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tw_tab, tt)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
+    if (!p->wide.empty() && (st = dev_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
     size_t ycount = 0;
     if (!small) ycount = (size_t)M;
     p->y_stride = (size_t)M * (size_t)std::max(1, std::min<int>(p->wide_G, (int)wide.size()));
@@ -403,6 +433,7 @@ Params base_params(const cwt_plan* p) {
     Params P{};
     P.Fp = p->d_Fp;
     P.Fp_out = p->d_Fp;
+    P.Ft = p->d_Ft;
     P.Y = p->d_Y;
     P.partials = p->d_partials;
     P.tw_lo = p->d_tw_lo;
@@ -515,6 +546,16 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, s,
                          CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
             return st;
+    }
+
+    // the wide scales' pass 1 reads the spectrum column by column: transpose it once
+    if (!p->wide.empty()) {
+        const int L = 1 << p->wide_logl;
+        const int A = (int)(p->M >> p->wide_logl);
+        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
+        k_spec_transpose<<<dim3((L + 31) / 32, (A + 31) / 32), dim3(32, 8), 0, s>>>(p->d_Fp, p->d_Ft, (int)p->M, L, A);
+        CWT_CUDA(p, cudaGetLastError());
+        lt.done();
     }
 
     // 2-3. band scales (one launch per DFT length) and wide-scale batches

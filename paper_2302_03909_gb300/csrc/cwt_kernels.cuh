@@ -60,6 +60,7 @@ struct Job {
 
 struct Params {
     const float2* Fp;        // F(m) = sum_n f(n) e^{+2 pi i m n / M}, m in [0, M/2]
+    const float2* Ft;        // wide pass 1: Ft[b A + a] = F(k), k = b + L a over all M unsigned bins
     float2* Fp_out;          // forward pass sink
     float2* Y;               // pass-1 -> pass-2 intermediate, [job][b][d]
     const void* signal;      // N samples, f32 or f64
@@ -118,21 +119,33 @@ __device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float h
     return g.amp * (expf(-0.5f * t * t) - expf(fmaf(-0.5f * v, v, -half_w0sq)));
 }
 
+// F is re-read by every scale: keep it in L2 (evict-last)
+__device__ __forceinline__ float2 ld_keep(const float2* q) {
+    uint64_t pol;
+    float2 v;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(q), "l"(pol));
+    return v;
+}
+
 // F at the signed bin k: F(-k) = conj F(k) for a real signal
 __device__ __forceinline__ float2 spec_at(const float2* __restrict__ Fp, int k) {
-    float2 f = __ldg(&Fp[k >= 0 ? k : -k]);
+    float2 f = ld_keep(&Fp[k >= 0 ? k : -k]);
     return make_float2(f.x, k >= 0 ? f.y : -f.y);
 }
 
-// Z(k) of a job (the pointwise product of Eq. 10, scaled)
-__device__ __forceinline__ float2 band_value(const Params& p, const Job& J, int k) {
-    float2 f = spec_at(p.Fp, k);
+// Z(k) of a job (the pointwise product of Eq. 10, scaled) given f = F(k)
+__device__ __forceinline__ float2 band_value_f(const Params& p, const Job& J, int k, float2 f) {
     float g0 = psi_gen(J.g[0], p.wavelet, p.half_w0sq, k);
     if (wav_real(p.wavelet)) {
         float g1 = J.g[1].row >= 0 ? psi_gen(J.g[1], p.wavelet, p.half_w0sq, k) : 0.f;
         return make_float2(fmaf(f.x, g0, -f.y * g1), fmaf(f.x, g1, f.y * g0));
     }
     return make_float2(f.x * g0, f.y * g0);
+}
+
+__device__ __forceinline__ float2 band_value(const Params& p, const Job& J, int k) {
+    return band_value_f(p, J, k, spec_at(p.Fp, k));
 }
 
 __device__ __forceinline__ float load_signal(const Params& p, int n) {
@@ -542,16 +555,18 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_
 struct Wide1Fill {
     const Params* p;
     const Job* J;
-    int b0, L;
+    int b0, L, A;
     template <int R>
     __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
         const int half = p->M >> 1;
         const int kend = J->k_lo + J->K;
+        const float2* col = p->Ft + (int64_t)(b0 + t) * A;   // column b of the spectrum, contiguous in a
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int k = b0 + t + L * (j + r * stride);      // unsigned bin in [0, M)
+            const int a = j + r * stride;
+            const int k = b0 + t + L * a;                      // unsigned bin in [0, M)
             const int ks = k <= half ? k : k - p->M;
-            v[r] = (ks >= J->k_lo && ks < kend) ? band_value(*p, *J, ks) : make_float2(0.f, 0.f);
+            v[r] = (ks >= J->k_lo && ks < kend) ? band_value_f(*p, *J, ks, __ldg(&col[a])) : make_float2(0.f, 0.f);
         }
     }
 };
@@ -600,7 +615,7 @@ __global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_
     if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
     __syncthreads();
     const int b0 = blockIdx.x * T;
-    Wide1Fill fill{&p, &sJ, b0, L};
+    Wide1Fill fill{&p, &sJ, b0, L, 1 << LOGA};
     YOut<true> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b0, 0, 1 << LOGA, 1};
     cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
 }
@@ -628,9 +643,10 @@ __global__ void __launch_bounds__(T * max_bfly(LOGL1, MAXLR), min_blocks(T * max
     const int kb0 = J.k_lo + ((b - J.k_lo) & (L - 1));      // first band bin = b mod L
     const int khi = J.k_lo + J.K - 1;
     const int a0 = (kb0 - b) / L;                             // exact: kb0 = b (mod L)
+    const float2* col = p.Ft + (int64_t)b * A;                // unsigned bin b + L a at col[a mod A]
     for (int i = threadIdx.x; i < L1; i += NT) {
         const int k = kb0 + L * i;
-        Zs[i] = k <= khi ? band_value(p, J, k) : make_float2(0.f, 0.f);
+        Zs[i] = k <= khi ? band_value_f(p, J, k, __ldg(&col[(a0 + i) & (A - 1)])) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     BandFill<LOGL1> fill{&p, Zs, a0, (uint32_t)L, d0};
