@@ -31,9 +31,10 @@ constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide 
 // ----------------------------------------------------------- launch shapes
 
 // tiles of T columns per CTA of the W-writing kernels: as many as keep the
-// grid at >= kMinCtas CTAs, at most kMaxD
+// grid at >= kMinCtas CTAs (two per SM: the band value table and the job set-up
+// are paid once per CTA), at most kMaxD
 constexpr int kMaxD = 8;
-constexpr int kMinCtas = 152 * 4;
+constexpr int kMinCtas = 152 * 2;
 int pick_D(int64_t tiles_total) {
     int64_t d = tiles_total / kMinCtas;
     return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxD, d));
