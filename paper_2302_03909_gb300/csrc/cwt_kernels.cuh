@@ -234,9 +234,15 @@ __host__ __device__ constexpr int stage_logr(int logl, int s, int maxlr = 5) {
 __host__ __device__ constexpr int stage_logns(int logl, int s, int maxlr = 5) {
     return s == 0 ? 0 : stage_logns(logl, s - 1, maxlr) + stage_logr(logl, s - 1, maxlr);
 }
-// butterflies of the last (smallest-radix) stage = threads per column
+// butterflies of the last (smallest-radix) stage
 __host__ __device__ constexpr int max_bfly(int logl, int maxlr = 5) {
     return 1 << (logl - stage_logr(logl, n_stages(logl, maxlr) - 1, maxlr));
+}
+// threads per column = butterflies of the first (largest-radix) stage; a
+// thread takes NB / col_threads butterflies of a later stage, so that every
+// thread holds the same number of values in every stage
+__host__ __device__ constexpr int col_threads(int logl, int maxlr = 5) {
+    return 1 << (logl - stage_logr(logl, 0, maxlr));
 }
 // odd smem row stride for T columns (bank spread for both thread mappings)
 __host__ __device__ constexpr int row_stride(int T) { return T == 1 ? 1 : ((T & 1) ? T : T + 1); }
@@ -278,20 +284,28 @@ __device__ __forceinline__ void stage_store(const float2* v, float2* buf, int j,
     for (int r = 0; r < St::R; r++) buf[(base + r * St::NS) * TT + t] = v[r];
 }
 
-// Middle stage S (0 < S < NST - 1): load, twiddle, DFT, exchange.
+// Middle stage S (0 < S < NST - 1): load, twiddle, DFT, exchange.  Each
+// thread holds its NB / P butterflies across the barrier.
 template <int LOGL, int S, int T, int TT, int MAXLR>
 __device__ __forceinline__ void cta_mid_stage(float2* buf, const float2* __restrict__ tw_tab, int tlim) {
     using St = Stage<LOGL, S, MAXLR>;
+    constexpr int P = col_threads(LOGL, MAXLR), NBT = St::NB / P;
     __syncthreads();
     const int t = threadIdx.x % T, j = threadIdx.x / T;
-    float2 v[St::R];
-    const bool act = j < St::NB && t < tlim;
+    float2 v[NBT][St::R];
+    const bool act = t < tlim;
     if (act) {
-        stage_load<LOGL, S, TT, MAXLR>(v, buf, j, t, tw_tab);
-        dft<St::R>(v);
+#pragma unroll
+        for (int q = 0; q < NBT; q++) {
+            stage_load<LOGL, S, TT, MAXLR>(v[q], buf, j + q * P, t, tw_tab);
+            dft<St::R>(v[q]);
+        }
     }
     __syncthreads();
-    if (act) stage_store<LOGL, S, TT, MAXLR>(v, buf, j, t);
+    if (act) {
+#pragma unroll
+        for (int q = 0; q < NBT; q++) stage_store<LOGL, S, TT, MAXLR>(v[q], buf, j + q * P, t);
+    }
 }
 
 template <int LOGL, int S, int NST, int T, int TT, int MAXLR>
@@ -334,13 +348,17 @@ __device__ __forceinline__ void cta_fft(float2* buf, const float2* __restrict__ 
         cta_mid_stages<LOGL, 1, NST, T, TT, MAXLR>(buf, tw_tab, tlim);
         __syncthreads();
         using SL = Stage<LOGL, NST - 1, MAXLR>;
-        const int t = LAST_JFAST ? tid / SL::NB : tid % T;
-        const int j = LAST_JFAST ? tid % SL::NB : tid / T;
-        if (j < SL::NB && t < tlim) {
-            float2 v[SL::R];
-            stage_load<LOGL, NST - 1, TT, MAXLR>(v, buf, j, t, tw_tab);
-            dft<SL::R>(v);
-            out(v, j, t, SL::NB);
+        constexpr int P = col_threads(LOGL, MAXLR);
+        const int t = LAST_JFAST ? tid / P : tid % T;
+        const int j = LAST_JFAST ? tid % P : tid / T;
+        if (t < tlim) {
+#pragma unroll
+            for (int jj = j; jj < SL::NB; jj += P) {
+                float2 v[SL::R];
+                stage_load<LOGL, NST - 1, TT, MAXLR>(v, buf, jj, t, tw_tab);
+                dft<SL::R>(v);
+                out(v, jj, t, SL::NB);
+            }
         }
     }
 }
@@ -519,10 +537,10 @@ struct BandFill {
 // run time): the band values, the job descriptor and the power reduction are
 // paid once per CTA.
 template <int LOGL, int T, bool CROP, int RD = 1, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR)))
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
     k_band(Params p) {
     constexpr int L = 1 << LOGL;
-    constexpr int NT = T * max_bfly(LOGL, MAXLR);
+    constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + RD * L;
@@ -607,8 +625,8 @@ struct YOut {
 
 // grid (L / T, jobs in batch): T columns b of the A-point DFTs of one job
 template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_bfly(LOGA, MAXLR))) k_wide1(Params p) {
-    constexpr int NT = T * max_bfly(LOGA, MAXLR);
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_wide1(Params p) {
+    constexpr int NT = T * col_threads(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
     __shared__ Job sJ;
@@ -625,10 +643,10 @@ __global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_
 // A-point DFT is itself a band tile of L1 >= P_b points over A1 = A / L1
 // columns d1 (d = d1 + A1 c1).  grid (L * tiles_per_b, jobs in batch).
 template <int LOGL1, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL1, MAXLR), min_blocks(T * max_bfly(LOGL1, MAXLR)))
+__global__ void __launch_bounds__(T * col_threads(LOGL1, MAXLR), min_blocks(T * col_threads(LOGL1, MAXLR)))
     k_wide1p(Params p, int L, int tiles_per_b) {
     constexpr int L1 = 1 << LOGL1;
-    constexpr int NT = T * max_bfly(LOGL1, MAXLR);
+    constexpr int NT = T * col_threads(LOGL1, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L1;
@@ -670,9 +688,9 @@ struct YFill {
 // grid (A / (T D), jobs in batch): D = p.D tiles of T columns d of the
 // L-point DFTs over b
 template <int LOGL, int T, bool CROP, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR)))
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
     k_wide2(Params p) {
-    constexpr int NT = T * max_bfly(LOGL, MAXLR);
+    constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     __shared__ double red[2 * ((NT + 31) / 32)];
     __shared__ Job sJ;
@@ -723,8 +741,8 @@ struct FOut {
 
 // pass 1 of the forward: grid L / T, A-point DFTs of the columns b
 template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_bfly(LOGA, MAXLR))) k_fwd1(Params p) {
-    constexpr int NT = T * max_bfly(LOGA, MAXLR);
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_fwd1(Params p) {
+    constexpr int NT = T * col_threads(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
     const int b0 = blockIdx.x * T;
@@ -735,8 +753,8 @@ __global__ void __launch_bounds__(T * max_bfly(LOGA, MAXLR), min_blocks(T * max_
 
 // pass 2 of the forward (or the whole forward when A = 1): grid A / T
 template <int LOGL, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * max_bfly(LOGL, MAXLR), min_blocks(T * max_bfly(LOGL, MAXLR))) k_fwd2(Params p) {
-    constexpr int NT = T * max_bfly(LOGL, MAXLR);
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR))) k_fwd2(Params p) {
+    constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     const int d0 = blockIdx.x * T;
     FOut out{p.Fp_out, p.A, d0, p.M >> 1};

@@ -10,7 +10,8 @@
 
 namespace cwtk {
 
-// threads per CTA are T * max_bfly(LOGL); aim at 256 threads (128 for one-stage DFTs)
+// T columns per CTA: T * max_bfly(LOGL) ~ 256 (128 for one-stage DFTs); the CTA
+// runs T * col_threads(LOGL) threads
 constexpr int kThreadsTarget = 256;
 // (three-stage DFTs keep 2 columns, 1 at L = 8192, so 128 registers fit)
 constexpr int band_T(int logl) {
@@ -33,17 +34,17 @@ using KernFnP = void (*)(Params, int, int);
 struct EntryP { KernFnP fn; int T, NT, logl; };
 
 template <int LOGL, int T, bool CROP, int RD = 1>
-Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, T, T * max_bfly(LOGL), LOGL}; }
+Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T, bool CROP>
-Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * max_bfly(LOGL), LOGL}; }
+Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * max_bfly(LOGL), LOGL}; }
+EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 
 struct Tables {
     Entry band[kLmaxLog + 1][2];            // [log2 L][crop]
