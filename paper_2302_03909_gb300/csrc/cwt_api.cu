@@ -191,7 +191,7 @@ void free_plan(cwt_plan* p) {
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Y,
+    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Zt, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
@@ -323,6 +323,8 @@ cwt_status build_plan(cwt_plan* p) {
             g.ntiles += per_job;
             assign_parts(J, per_job);
             g.bytes += job_rows(J) * out_row_bytes(p) + 8.0 * J.K;
+            J.zt_off = (int32_t)p->zt_count;
+            p->zt_count += J.K;
             p->jobs.push_back(J);
         }
         p->groups.push_back(g);
@@ -394,6 +396,7 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tw_tab, tt)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
+    if ((st = dev_alloc(p, &p->d_Zt, (size_t)p->zt_count)) != CWT_OK) return st;
     if (!p->wide.empty() && (st = dev_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
     size_t ycount = 0;
     if (!small) ycount = (size_t)M;
@@ -435,6 +438,7 @@ Params base_params(const cwt_plan* p) {
     P.Fp = p->d_Fp;
     P.Fp_out = p->d_Fp;
     P.Ft = p->d_Ft;
+    P.Zt = p->d_Zt;
     P.Y = p->d_Y;
     P.partials = p->d_partials;
     P.tw_lo = p->d_tw_lo;
@@ -448,6 +452,11 @@ Params base_params(const cwt_plan* p) {
     P.wavelet = p->wavelet;
     P.sig_f64 = p->opts.input_dtype == CWT_INPUT_F64;
     P.half_w0sq = (float)(0.5 * p->opts.omega0 * p->opts.omega0);
+    // the Morlet's correction term is below eps_trunc (relative to the spectrum's
+    // peak, ~1) where (v^2 + omega0^2) / 2 > -ln(eps); never skipped without truncation
+    const double cv2 = p->opts.eps_trunc > 0.0 ? -2.0 * std::log(p->opts.eps_trunc) - p->opts.omega0 * p->opts.omega0
+                                               : 1e30;
+    P.corr_v2 = (float)std::min(1e30, std::max(0.0, cv2));
     return P;
 }
 
@@ -547,6 +556,14 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, s,
                          CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
             return st;
+    }
+
+    // the band jobs' values Z(k), once per call (each band CTA reads its job's table)
+    if (p->n_band_jobs > 0) {
+        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
+        k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, s>>>(P);
+        CWT_CUDA(p, cudaGetLastError());
+        lt.done();
     }
 
     // the wide scales' pass 1 reads the spectrum column by column: transpose it once

@@ -55,11 +55,12 @@ struct Job {
     int32_t k_lo;       // signed lowest bin of the band
     int32_t K;          // band width in bins (1..M)
     int32_t tile0;      // first tile of this job within its launch
-    int32_t pad_;
+    int32_t zt_off;     // band jobs: offset of the job's band values Z(k_lo + i) in Params::Zt
 };
 
 struct Params {
     const float2* Fp;        // F(m) = sum_n f(n) e^{+2 pi i m n / M}, m in [0, M/2]
+    const float2* Zt;        // band jobs' values Z(k_lo + i), i < K, computed once per call
     const float2* Ft;        // wide pass 1: Ft[b A + a] = F(k), k = b + L a over all M unsigned bins
     float2* Fp_out;          // forward pass sink
     float2* Y;               // pass-1 -> pass-2 intermediate, [job][b][d]
@@ -80,6 +81,8 @@ struct Params {
     int32_t sig_f64;
     int32_t do_power;
     float half_w0sq;         // omega0^2 / 2
+    float corr_v2;           // Morlet: the correction e^{-(v^2 + omega0^2)/2} is below the band
+                             // truncation threshold for v^2 >= corr_v2
 };
 
 // ------------------------------------------------------------------ helpers
@@ -97,13 +100,21 @@ __device__ __forceinline__ float2 tw_m(const Params& p, uint32_t j) {
     return cmul(hi, lo);
 }
 
+// e^x = 2^(x log2 e) with the hardware base-2 exponential (relative error
+// about 2^-22 for the arguments that matter here, |x| < 40; flushes to 0 below)
+__device__ __forceinline__ float exp_fast(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.44269504088896341f));
+    return y;
+}
+
 // amp * psi_hat(alpha k) for the signed bin k (Table 2 spectra)
-__device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float half_w0sq, int k) {
+__device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float half_w0sq, float corr_v2, int k) {
     float kf = (float)k;
     float v = fmaf(g.a_hi, kf, g.a_lo * kf);
     if (wavelet == WAV_GDW) {
         float v2 = v * v;
-        return g.amp * v2 * expf(-v2);
+        return g.amp * v2 * exp_fast(-v2);
     }
     if (wavelet == WAV_CBSW) {                              // 64 C_N sin^6(u/2) / u^4
         if (v == 0.f) return 0.f;
@@ -112,11 +123,13 @@ __device__ __forceinline__ float psi_gen(const ScaleGen& g, int wavelet, float h
     }
     if (wavelet == WAV_CWGDW) {                             // sqrt(2 pi) C_N u (u cosh u - sinh u) e^{-u^2/2}
         const float h = -0.5f * v * v;
-        return g.amp * v * 0.5f * ((v - 1.f) * expf(v + h) + (v + 1.f) * expf(h - v));
+        return g.amp * v * 0.5f * ((v - 1.f) * exp_fast(v + h) + (v + 1.f) * exp_fast(h - v));
     }
     float d = (float)(k - g.k0_int) - g.k0_frac;           // k - omega0/alpha, exact integer part
     float t = fmaf(g.a_hi, d, g.a_lo * d);                 // alpha k - omega0
-    return g.amp * (expf(-0.5f * t * t) - expf(fmaf(-0.5f * v, v, -half_w0sq)));
+    const float v2 = v * v;
+    const float corr = v2 < corr_v2 ? exp_fast(fmaf(-0.5f, v2, -half_w0sq)) : 0.f;
+    return g.amp * (exp_fast(-0.5f * t * t) - corr);
 }
 
 // F is re-read by every scale: keep it in L2 (evict-last)
@@ -136,9 +149,9 @@ __device__ __forceinline__ float2 spec_at(const float2* __restrict__ Fp, int k) 
 
 // Z(k) of a job (the pointwise product of Eq. 10, scaled) given f = F(k)
 __device__ __forceinline__ float2 band_value_f(const Params& p, const Job& J, int k, float2 f) {
-    float g0 = psi_gen(J.g[0], p.wavelet, p.half_w0sq, k);
+    float g0 = psi_gen(J.g[0], p.wavelet, p.half_w0sq, p.corr_v2, k);
     if (wav_real(p.wavelet)) {
-        float g1 = J.g[1].row >= 0 ? psi_gen(J.g[1], p.wavelet, p.half_w0sq, k) : 0.f;
+        float g1 = J.g[1].row >= 0 ? psi_gen(J.g[1], p.wavelet, p.half_w0sq, p.corr_v2, k) : 0.f;
         return make_float2(fmaf(f.x, g0, -f.y * g1), fmaf(f.x, g1, f.y * g0));
     }
     return make_float2(f.x * g0, f.y * g0);
@@ -553,7 +566,7 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
     const Job& J = sJ;
     const int dbase = (tile - J.tile0) * T * p.D;
     for (int i = threadIdx.x; i < RD * L; i += NT)
-        Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
+        Zs[i] = i < J.K ? __ldg(&p.Zt[J.zt_off + i]) : make_float2(0.f, 0.f);
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
     for (int q = 0; q < p.D; q++) {
@@ -565,6 +578,15 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
         cta_fft<LOGL, T, NT, false, MAXLR>(buf, p.tw_tab, fill, out, min(T, p.A - d0));
     }
     write_partials<NT>(p, J, out, tile - J.tile0, red);
+}
+
+// The band values of every band job, once per call: grid = band jobs.
+static __global__ void __launch_bounds__(256) k_band_table(Params p) {
+    __shared__ Job sJ;
+    if (threadIdx.x == 0) sJ = p.jobs[blockIdx.x];
+    __syncthreads();
+    float2* zt = const_cast<float2*>(p.Zt) + sJ.zt_off;
+    for (int i = threadIdx.x; i < sJ.K; i += 256) zt[i] = band_value(p, sJ, sJ.k_lo + i);
 }
 
 // ------------------------------------------------------------ wide pass 1
