@@ -135,6 +135,104 @@ static __global__ void k_spec_transpose(const float2* __restrict__ Fp, float2* _
     }
 }
 
+// ------------------------------------------------ zero boundary, short wavelets
+//
+// For a scale whose dilated wavelet is negligible beyond E samples (E <= N/4,
+// E <= M - N), the zero-padded transform (length M) restricted to n < N is the
+// linear convolution of f with h(j) = sqrt(w~ dx) psi(w~ j) (Eq. 7), and the
+// periodic N-point transform differs from it only by the wrapped terms:
+//   W_zero(n) = W_N(n) - sum_{j=n+1}^{E} h(j) f(N + n - j),          n < E,
+//   W_zero(n) = W_N(n) - sum_{j=-E}^{n-N} h(j) f(n - N - j),          n >= N - E.
+// Such rows are computed by a periodic child plan and corrected here.
+
+struct EdgeRow { int32_t E; int32_t h_off; };
+constexpr int kEdgeThreads = 256;
+constexpr int64_t kEdgeMax = 4096;           // largest E handled this way
+
+// grid (blocks per row, rows): thread idx < 2E corrects one edge output of
+// the row; with power, each block records its change of sum |W|^2
+template <bool CPLX>
+static __global__ void __launch_bounds__(kEdgeThreads)
+    k_edge_fix(const void* __restrict__ signal, int sig_f64, int64_t N, void* W, const float2* __restrict__ h,
+               const EdgeRow* __restrict__ rows, double* __restrict__ delta, int do_power) {
+    __shared__ double red[2 * (kEdgeThreads / 32)];
+    const int r = blockIdx.y;
+    const EdgeRow er = rows[r];
+    const int idx = blockIdx.x * kEdgeThreads + threadIdx.x;
+    float dpow = 0.f;
+    if (idx < 2 * er.E) {
+        const float2* hr = h + er.h_off + er.E;       // hr[j], j in [-E, E]
+        int64_t n, fbase;
+        int jlo, jhi;
+        if (idx < er.E) {
+            n = idx;
+            jlo = idx + 1;
+            jhi = er.E;
+            fbase = N + n;
+        } else {
+            n = N - 2 * (int64_t)er.E + idx;
+            jlo = -er.E;
+            jhi = (int)(n - N);
+            fbase = n - N;
+        }
+        float cr = 0.f, ci = 0.f;
+        for (int j = jlo; j <= jhi; j++) {
+            const int64_t m = fbase - j;                 // in [0, N)
+            const float fv = sig_f64 ? (float)__ldg(&((const double*)signal)[m]) : __ldg(&((const float*)signal)[m]);
+            const float2 hv = __ldg(&hr[j]);
+            cr = fmaf(hv.x, fv, cr);
+            ci = fmaf(hv.y, fv, ci);
+        }
+        if constexpr (CPLX) {
+            float2* q = (float2*)W + (int64_t)r * N + n;
+            const float2 o = *q;
+            const float2 w = make_float2(o.x - cr, o.y - ci);
+            *q = w;
+            dpow = (w.x * w.x + w.y * w.y) - (o.x * o.x + o.y * o.y);
+        } else {
+            float* q = (float*)W + (int64_t)r * N + n;
+            const float o = *q, w = o - cr;
+            *q = w;
+            dpow = w * w - o * o;
+        }
+    }
+    if (do_power) {
+        double s0, s1;
+        block_sum2<kEdgeThreads>(dpow, 0.f, &s0, &s1, red);
+        if (threadIdx.x == 0) delta[(int64_t)r * gridDim.x + blockIdx.x] = s0;
+    }
+}
+
+// spectrum[r] += (sum of the row's block changes, fixed order) / N
+static __global__ void k_edge_power(const double* __restrict__ delta, int bpr, int64_t N, double* __restrict__ spectrum) {
+    if (threadIdx.x != 0) return;
+    double acc = 0.0;
+    for (int b = 0; b < bpr; b++) acc += delta[(int64_t)blockIdx.x * bpr + b];
+    spectrum[blockIdx.x] += acc / (double)N;
+}
+
+namespace {
+
+// half width (in units of x) beyond which |psi(x)| < ~1e-13: GDW (2 - x^2) e^{-x^2/4}
+// at x = 12.5, the Morlet's Gaussian envelope e^{-x^2/2} at x = 8.5
+double psi_support(int wavelet) { return wavelet == CWT_WAVELET_GDW ? 12.5 : 8.5; }
+
+int64_t edge_width(int wavelet, double wt) { return (int64_t)std::ceil(psi_support(wavelet) / wt) + 1; }
+
+// psi(x) of Table 2 (GDW, Morlet), FP64
+void psi_x(int wavelet, double omega0, double x, double* re, double* im) {
+    if (wavelet == CWT_WAVELET_GDW) {
+        *re = std::pow(18.0 * kPi, -0.25) * (2.0 - x * x) * std::exp(-0.25 * x * x);
+        *im = 0.0;
+        return;
+    }
+    const double cn = wavelet_cn(wavelet, omega0), env = std::exp(-0.5 * x * x);
+    *re = cn * (std::cos(omega0 * x) - std::exp(-0.5 * omega0 * omega0)) * env;
+    *im = -cn * std::sin(omega0 * x) * env;
+}
+
+}  // namespace
+
 // ====================================================================== plan
 
 
@@ -190,12 +288,19 @@ void free_plan(cwt_plan* p) {
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->child_stream) cudaStreamDestroy(p->child_stream);
+    if (p->ev_cfork) cudaEventDestroy(p->ev_cfork);
+    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Zt, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    void* edge[] = {p->d_edge_rows, p->d_edge_h, p->d_edge_delta};
+    for (void* q : edge)
+        if (q) cudaFree(q);
+    if (p->child) free_plan(p->child);
     delete p;
 }
 
@@ -244,15 +349,20 @@ cwt_status build_plan(cwt_plan* p) {
     bool full = p->opts.eps_trunc <= 0.0;
     if (!full) wavelet_band(p->wavelet, p->opts.omega0, p->opts.eps_trunc, &u_lo, &u_hi);
 
-    // jobs: GDW pairs (2i, 2i+1); Morlet one scale each
+    // jobs: real wavelets pair consecutive rows, the Morlet takes one row each;
+    // rows that a child plan computes are left out
     const int per = wav_real(p->wavelet) ? 2 : 1;
+    std::vector<int> own_rows;
+    for (int r = 0; r < p->S; r++)
+        if (r < p->child_r0 || r >= p->child_r0 + p->child_n) own_rows.push_back(r);
     std::vector<Job> all;
-    for (int s0 = 0; s0 < p->S; s0 += per) {
+    for (size_t i0 = 0; i0 < own_rows.size(); i0 += per) {
         Job J{};
         int64_t klo = 0, khi = -1;
         for (int q = 0; q < 2; q++) {
-            int s = s0 + q;
-            if (q < per && s < p->S) {
+            const size_t i = i0 + q;
+            const int s = i < own_rows.size() ? own_rows[i] : -1;
+            if (q < per && s >= 0) {
                 J.g[q] = make_gen(p, p->w_tilde[s], s);
                 int64_t a, b;
                 if (full) { a = -(M / 2) + 1; b = M / 2; }
@@ -405,10 +515,38 @@ cwt_status build_plan(cwt_plan* p) {
         ycount = std::max(ycount, p->y_stride * (size_t)std::min<size_t>(p->wide.size(), cwt_plan::kSide + 1));
     if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
+    if (p->child) {
+        std::vector<EdgeRow> er(p->child_n);
+        std::vector<float2> h;
+        int64_t emax = 0;
+        for (int i = 0; i < p->child_n; i++) {
+            const double wt = p->w_tilde[p->child_r0 + i];
+            const int64_t E = edge_width(p->wavelet, wt);
+            er[i] = {(int32_t)E, (int32_t)h.size()};
+            const double nrm = std::sqrt(wt * p->opts.dx);
+            for (int64_t j = -E; j <= E; j++) {
+                double re, im;
+                psi_x(p->wavelet, p->opts.omega0, wt * (double)j, &re, &im);
+                h.push_back(make_float2((float)(nrm * re), (float)(nrm * im)));
+            }
+            emax = std::max(emax, E);
+        }
+        p->edge_bpr = (int32_t)((2 * emax + kEdgeThreads - 1) / kEdgeThreads);
+        EdgeRow* d_er = nullptr;
+        if ((st = upload(p, &d_er, er)) != CWT_OK) return st;
+        p->d_edge_rows = d_er;
+        if ((st = upload(p, &p->d_edge_h, h)) != CWT_OK) return st;
+        if ((st = dev_alloc(p, &p->d_edge_delta, (size_t)p->child_n * p->edge_bpr)) != CWT_OK) return st;
+    }
 
     // side streams and events, and the shared-memory opt-in of every kernel the
     // plan launches, are set up here so that no call made while capturing needs them
     CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    if (p->child) {
+        CWT_CUDA(p, cudaStreamCreateWithFlags(&p->child_stream, cudaStreamNonBlocking));
+        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_cfork, cudaEventDisableTiming));
+        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
+    }
     for (int i = 0; i < cwt_plan::kSide; i++) {
         CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
         CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
@@ -536,6 +674,42 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     P.W = W;
     P.do_power = spectrum != nullptr;
 
+    // rows with short wavelet support: the periodic child plan and the edge
+    // correction, on their own stream from the start of the call
+    if (p->child) {
+        CWT_CUDA(p, cudaEventRecord(p->ev_cfork, s));
+        CWT_CUDA(p, cudaStreamWaitEvent(p->child_stream, p->ev_cfork, 0));
+        const size_t esz = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
+        void* Wc = (char*)W + (size_t)p->child_r0 * (size_t)p->N * esz;
+        double* sc = spectrum ? spectrum + p->child_r0 : nullptr;
+        if ((st = run_launches(p->child, signal, Wc, sc, p->child_stream)) != CWT_OK) return st;
+        {
+            LaunchTimer lt(p, CWT_KCLASS_BAND, 0.0, p->child_stream);
+            const dim3 grid((unsigned)p->edge_bpr, (unsigned)p->child_n);
+            const EdgeRow* rows = (const EdgeRow*)p->d_edge_rows;
+            const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
+            if (p->wavelet == CWT_WAVELET_MORLET)
+                k_edge_fix<true><<<grid, kEdgeThreads, 0, p->child_stream>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
+                                                                            p->d_edge_delta, sc != nullptr);
+            else
+                k_edge_fix<false><<<grid, kEdgeThreads, 0, p->child_stream>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
+                                                                             p->d_edge_delta, sc != nullptr);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
+        if (sc) {
+            LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, p->child_stream);
+            k_edge_power<<<p->child_n, 32, 0, p->child_stream>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
+        CWT_CUDA(p, cudaEventRecord(p->ev_cjoin, p->child_stream));
+    }
+    if (p->jobs.empty()) {                       // every row came from the child
+        if (p->child) CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_cjoin, 0));
+        return CWT_OK;
+    }
+
     // 1. forward transform F(m) = sum_n f(n) e^{+2 pi i m n / M}, m <= M/2
     if (p->fwd_small) {
         const Entry& e = tb.fwd_small[p->logM];
@@ -641,6 +815,8 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         CWT_CUDA(p, cudaEventRecord(p->ev_join[i - 1], streams[i]));
         CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i - 1], 0));
     }
+
+    if (p->child) CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_cjoin, 0));
 
     // 4. power spectrum: fixed-order reduction of the per-tile partials
     if (spectrum) {
@@ -769,6 +945,34 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         free_plan(p);
         return CWT_ERR_CUDA;
     }
+    // zero boundary with the default padding (M = 2N): a contiguous run of rows
+    // with short wavelet support goes to a periodic N-point child plan
+    if (boundary == CWT_BOUNDARY_ZERO && o.fft_len == 0 && is_pow2(N) && N >= 1024 &&
+        (wavelet == CWT_WAVELET_GDW || wavelet == CWT_WAVELET_MORLET)) {
+        const int64_t emax = std::min<int64_t>({kEdgeMax, N / 4, M - N});
+        int r0 = -1, r1 = -1;
+        bool contiguous = true;
+        for (int32_t i = 0; i < n_scales; i++) {
+            if (edge_width(wavelet, p->w_tilde[i]) > emax) continue;
+            if (r0 < 0) r0 = i;
+            else if (r1 != i) contiguous = false;
+            r1 = i + 1;
+        }
+        if (r0 >= 0 && contiguous) {
+            cwt_plan_opts co = o;
+            co.scale_unit = CWT_SCALE_W_TILDE;
+            co.fft_len = 0;
+            cwt_status cs = cwt_plan_create_ex(&p->child, N, p->w_tilde.data() + r0, r1 - r0, wavelet,
+                                               CWT_BOUNDARY_PERIODIC, &co);
+            if (cs != CWT_OK) {
+                free_plan(p);
+                return cs;
+            }
+            p->child_r0 = r0;
+            p->child_n = r1 - r0;
+            p->ws_bytes += p->child->ws_bytes;
+        }
+    }
     cwt_status st = build_plan(p);
     if (st != CWT_OK) {
         free_plan(p);
@@ -896,6 +1100,7 @@ cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable) {
     if (!plan->pending.empty()) cudaDeviceSynchronize();
     release_events(plan);
     plan->timing = enable != 0;
+    if (plan->child) cwt_plan_set_timing(plan->child, enable);
     for (int c = 0; c < CWT_KCLASS_COUNT; c++) {
         plan->t_ms[c] = 0.0;
         plan->t_launches[c] = 0;
@@ -916,9 +1121,15 @@ cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t cls, double* total_ms, in
         plan->t_bytes[r.cls] += r.bytes;
     }
     release_events(plan);
-    if (total_ms) *total_ms = plan->t_ms[cls];
-    if (launches) *launches = plan->t_launches[cls];
-    if (algorithmic_bytes) *algorithmic_bytes = plan->t_bytes[cls];
+    double cm = 0.0, cb = 0.0;
+    int64_t cn = 0;
+    if (plan->child) {
+        cwt_status st = cwt_plan_get_timing(plan->child, cls, &cm, &cn, &cb);
+        if (st != CWT_OK) return st;
+    }
+    if (total_ms) *total_ms = plan->t_ms[cls] + cm;
+    if (launches) *launches = plan->t_launches[cls] + cn;
+    if (algorithmic_bytes) *algorithmic_bytes = plan->t_bytes[cls] + cb;
     return CWT_OK;
 }
 

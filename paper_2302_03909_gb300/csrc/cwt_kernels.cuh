@@ -796,7 +796,7 @@ static __global__ void k_power_finalize(const double* __restrict__ partials, con
                                         const int32_t* __restrict__ cnt, int32_t S, int64_t N,
                                         double* __restrict__ spectrum) {
     int s = blockIdx.x;
-    if (s >= S) return;
+    if (s >= S || cnt[s] == 0) return;          // rows without partials belong to a child plan
     double acc = 0.0;
     for (int i = threadIdx.x; i < cnt[s]; i += 32) acc += partials[off[s] + i];
 #pragma unroll

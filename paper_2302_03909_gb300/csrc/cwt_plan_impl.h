@@ -81,6 +81,18 @@ struct cwt_plan {
     double t_bytes[CWT_KCLASS_COUNT] = {};
     double fwd_in_bytes = 0, fwd_out_bytes = 0;
 
+    // zero boundary: the rows child_r0 .. child_r0 + child_n - 1, whose wavelet
+    // support E (samples) is short, come from a periodic N-point child plan
+    // followed by an edge correction of their 2E outermost outputs
+    cwt_plan* child = nullptr;
+    int32_t child_r0 = 0, child_n = 0;
+    cudaStream_t child_stream = nullptr;  // the child's work, forked at the start of a call
+    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr;
+    int32_t edge_bpr = 0;                 // correction blocks per row
+    void* d_edge_rows = nullptr;          // per row: E and the offset of its h table
+    float2* d_edge_h = nullptr;           // h(j) = sqrt(w~ dx) psi(w~ j), j in [-E, E]
+    double* d_edge_delta = nullptr;       // per block: change of the row's sum of |W|^2
+
     std::string err;
 };
 

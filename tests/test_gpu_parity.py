@@ -241,3 +241,36 @@ def test_graph_replay_matches_direct_launches(env):
         torch.cuda.synchronize()
         assert torch.equal(W0, W2)
         plan.close()
+
+
+@pytest.mark.parametrize("N,wavelet,smin,smax,S,order,dtype", [
+    (4096, "gdw", 2.0, 40.0, 9, "asc", "f32"),          # every row short: the padded plan runs no job of its own
+    (1024, "morlet", 4.0, 60.0, 8, "asc", "f32"),       # E up to N/4 = 256, then the padded path
+    (1 << 15, "morlet", 4.0, 2e4, 14, "desc", "f32"),   # short rows at the end
+    (1 << 15, "gdw", 2.0, 2e4, 13, "shuffled", "f32"),  # short rows not contiguous: all padded
+    (1 << 14, "morlet", 4.0, 3000.0, 10, "asc", "f64"),
+])
+def test_zero_boundary_short_scales(env, N, wavelet, smin, smax, S, order, dtype):
+    """Zero boundary: rows whose wavelet is short are computed as N-point periodic
+    transforms with the wrapped edge terms removed; W and the power spectrum must
+    equal the zero-padded (M = 2N) FFTCWT of the oracle."""
+    _, _, orc = env
+    f = synth.lognormal_field(N, seed=N + S + 7)
+    sc = synth.log_scales(smin, smax, S)
+    if order == "desc":
+        sc = sc[::-1].copy()
+    elif order == "shuffled":
+        sc = sc[np.random.default_rng(1).permutation(S)]
+    W, spec, M = run_gpu(env, f, sc, wavelet, "zero", dtype=dtype)
+    assert M == 2 * N
+    fin = f if dtype == "f64" else f32(f)
+    ref = orc.cwt_fft(fin, sc, wavelet, M=M)
+    assert rel_l2(W, ref) <= TOL
+    for s in range(S):
+        assert np.linalg.norm(W[s] - ref[s]) / np.linalg.norm(ref[s]) <= 10 * TOL, s
+        # the corrected edges on their own
+        e = min(N // 8, 64)
+        edge = np.r_[0:e, N - e:N]
+        assert np.linalg.norm(W[s, edge] - ref[s, edge]) <= 10 * TOL * np.linalg.norm(ref[s]) + 1e-12, s
+    P = orc.wavelet_power(ref)
+    assert np.max(np.abs(spec - P) / P) < 1e-4
