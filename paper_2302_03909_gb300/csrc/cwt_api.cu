@@ -149,51 +149,95 @@ struct EdgeRow { int32_t E; int32_t h_off; };
 constexpr int kEdgeThreads = 256;
 constexpr int64_t kEdgeMax = 4096;           // largest E handled this way
 
-// grid (blocks per row, rows): thread idx < 2E corrects one edge output of
-// the row; with power, each block records its change of sum |W|^2
+// grid (2 * chunks, rows): block b corrects outputs i in [256 c, 256 c + 256) of
+// one edge (b even: left, n = i; b odd: right, n = N - E + i), i < E.  With
+// k the term index, the two sums are sliding dot products:
+//   left:  corr(i) = sum_{k=0}^{E-1-i} f(N-1-k) h(i+1+k),
+//   right: corr(i) = sum_{k=0}^{i}     h(-E+k)  f(i-k),
+// taken over tiles of kEdgeKT terms staged in shared memory.  With power,
+// each block records its change of sum |W|^2.
+constexpr int kEdgeKT = 512;
+
+__device__ __forceinline__ float load_f(const void* signal, int f64, int64_t m) {
+    return f64 ? (float)__ldg(&((const double*)signal)[m]) : __ldg(&((const float*)signal)[m]);
+}
+
 template <bool CPLX>
 static __global__ void __launch_bounds__(kEdgeThreads)
     k_edge_fix(const void* __restrict__ signal, int sig_f64, int64_t N, void* W, const float2* __restrict__ h,
                const EdgeRow* __restrict__ rows, double* __restrict__ delta, int do_power) {
+    __shared__ float fs[kEdgeKT + kEdgeThreads];
+    __shared__ float2 hs[kEdgeKT + kEdgeThreads];
     __shared__ double red[2 * (kEdgeThreads / 32)];
     const int r = blockIdx.y;
     const EdgeRow er = rows[r];
-    const int idx = blockIdx.x * kEdgeThreads + threadIdx.x;
+    const int E = er.E;
+    const bool left = (blockIdx.x & 1) == 0;
+    const int i0 = (blockIdx.x >> 1) * kEdgeThreads;
+    const int i = i0 + threadIdx.x;
+    const float2* hr = h + er.h_off + E;              // hr[j], j in [-E, E]
     float dpow = 0.f;
-    if (idx < 2 * er.E) {
-        const float2* hr = h + er.h_off + er.E;       // hr[j], j in [-E, E]
-        int64_t n, fbase;
-        int jlo, jhi;
-        if (idx < er.E) {
-            n = idx;
-            jlo = idx + 1;
-            jhi = er.E;
-            fbase = N + n;
-        } else {
-            n = N - 2 * (int64_t)er.E + idx;
-            jlo = -er.E;
-            jhi = (int)(n - N);
-            fbase = n - N;
-        }
+    if (i0 < E) {                                     // block-uniform
+        // terms of this block: left k in [0, E - 1 - i0], right k in [0, i0 + 255]
+        const int kmax = left ? E - 1 - i0 : min(i0 + kEdgeThreads - 1, E - 1);
         float cr = 0.f, ci = 0.f;
-        for (int j = jlo; j <= jhi; j++) {
-            const int64_t m = fbase - j;                 // in [0, N)
-            const float fv = sig_f64 ? (float)__ldg(&((const double*)signal)[m]) : __ldg(&((const float*)signal)[m]);
-            const float2 hv = __ldg(&hr[j]);
-            cr = fmaf(hv.x, fv, cr);
-            ci = fmaf(hv.y, fv, ci);
+        for (int k0 = 0; k0 <= kmax; k0 += kEdgeKT) {
+            __syncthreads();
+            if (left) {
+                // fs[kk] = f(N-1-k0-kk), hs[u] = h(i0+1+k0+u), u < KT + 255
+                for (int u = threadIdx.x; u < kEdgeKT; u += kEdgeThreads) {
+                    const int k = k0 + u;
+                    fs[u] = k <= kmax ? load_f(signal, sig_f64, N - 1 - k) : 0.f;
+                }
+                for (int u = threadIdx.x; u < kEdgeKT + kEdgeThreads; u += kEdgeThreads) {
+                    const int j = i0 + 1 + k0 + u;
+                    hs[u] = j <= E ? __ldg(&hr[j]) : make_float2(0.f, 0.f);
+                }
+            } else {
+                // hs[kk] = h(-E+k0+kk), fs[u] = f(i0 - k0 - KT + 1 + u), u < KT + 255
+                for (int u = threadIdx.x; u < kEdgeKT; u += kEdgeThreads) {
+                    const int k = k0 + u;
+                    hs[u] = k <= kmax ? __ldg(&hr[-E + k]) : make_float2(0.f, 0.f);
+                }
+                for (int u = threadIdx.x; u < kEdgeKT + kEdgeThreads; u += kEdgeThreads) {
+                    const int m = i0 - k0 - kEdgeKT + 1 + u;
+                    fs[u] = (m >= 0 && m < E) ? load_f(signal, sig_f64, m) : 0.f;
+                }
+            }
+            __syncthreads();
+            if (i < E) {
+                const int kend = min(kEdgeKT, (left ? E - 1 - i : i) - k0 + 1);   // terms of this thread in the tile
+                const int t = threadIdx.x;
+#pragma unroll 8
+                for (int kk = 0; kk < kend; kk++) {
+                    float fv;
+                    float2 hv;
+                    if (left) {
+                        fv = fs[kk];
+                        hv = hs[t + kk];
+                    } else {
+                        hv = hs[kk];
+                        fv = fs[t - kk + kEdgeKT - 1];
+                    }
+                    cr = fmaf(hv.x, fv, cr);
+                    ci = fmaf(hv.y, fv, ci);
+                }
+            }
         }
-        if constexpr (CPLX) {
-            float2* q = (float2*)W + (int64_t)r * N + n;
-            const float2 o = *q;
-            const float2 w = make_float2(o.x - cr, o.y - ci);
-            *q = w;
-            dpow = (w.x * w.x + w.y * w.y) - (o.x * o.x + o.y * o.y);
-        } else {
-            float* q = (float*)W + (int64_t)r * N + n;
-            const float o = *q, w = o - cr;
-            *q = w;
-            dpow = w * w - o * o;
+        if (i < E) {
+            const int64_t n = left ? (int64_t)i : N - E + i;
+            if constexpr (CPLX) {
+                float2* q = (float2*)W + (int64_t)r * N + n;
+                const float2 o = *q;
+                const float2 w = make_float2(o.x - cr, o.y - ci);
+                *q = w;
+                dpow = (w.x * w.x + w.y * w.y) - (o.x * o.x + o.y * o.y);
+            } else {
+                float* q = (float*)W + (int64_t)r * N + n;
+                const float o = *q, w = o - cr;
+                *q = w;
+                dpow = w * w - o * o;
+            }
         }
     }
     if (do_power) {
@@ -288,9 +332,6 @@ void free_plan(cwt_plan* p) {
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->child_stream) cudaStreamDestroy(p->child_stream);
-    if (p->ev_cfork) cudaEventDestroy(p->ev_cfork);
-    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Zt, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
@@ -531,7 +572,7 @@ cwt_status build_plan(cwt_plan* p) {
             }
             emax = std::max(emax, E);
         }
-        p->edge_bpr = (int32_t)((2 * emax + kEdgeThreads - 1) / kEdgeThreads);
+        p->edge_bpr = (int32_t)(2 * ((emax + kEdgeThreads - 1) / kEdgeThreads));
         EdgeRow* d_er = nullptr;
         if ((st = upload(p, &d_er, er)) != CWT_OK) return st;
         p->d_edge_rows = d_er;
@@ -542,11 +583,7 @@ cwt_status build_plan(cwt_plan* p) {
     // side streams and events, and the shared-memory opt-in of every kernel the
     // plan launches, are set up here so that no call made while capturing needs them
     CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-    if (p->child) {
-        CWT_CUDA(p, cudaStreamCreateWithFlags(&p->child_stream, cudaStreamNonBlocking));
-        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_cfork, cudaEventDisableTiming));
-        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
-    }
+
     for (int i = 0; i < cwt_plan::kSide; i++) {
         CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
         CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming));
@@ -674,41 +711,36 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     P.W = W;
     P.do_power = spectrum != nullptr;
 
-    // rows with short wavelet support: the periodic child plan and the edge
-    // correction, on their own stream from the start of the call
+    // rows with short wavelet support: the periodic child plan (with its own
+    // side streams) and the edge correction, first on the call's stream; running
+    // it beside this plan's streams put too many intermediates in flight for L2
     if (p->child) {
-        CWT_CUDA(p, cudaEventRecord(p->ev_cfork, s));
-        CWT_CUDA(p, cudaStreamWaitEvent(p->child_stream, p->ev_cfork, 0));
         const size_t esz = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
         void* Wc = (char*)W + (size_t)p->child_r0 * (size_t)p->N * esz;
         double* sc = spectrum ? spectrum + p->child_r0 : nullptr;
-        if ((st = run_launches(p->child, signal, Wc, sc, p->child_stream)) != CWT_OK) return st;
+        if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
         {
-            LaunchTimer lt(p, CWT_KCLASS_BAND, 0.0, p->child_stream);
+            LaunchTimer lt(p, CWT_KCLASS_BAND, 0.0, s);
             const dim3 grid((unsigned)p->edge_bpr, (unsigned)p->child_n);
             const EdgeRow* rows = (const EdgeRow*)p->d_edge_rows;
             const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
             if (p->wavelet == CWT_WAVELET_MORLET)
-                k_edge_fix<true><<<grid, kEdgeThreads, 0, p->child_stream>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
+                k_edge_fix<true><<<grid, kEdgeThreads, 0, s>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
                                                                             p->d_edge_delta, sc != nullptr);
             else
-                k_edge_fix<false><<<grid, kEdgeThreads, 0, p->child_stream>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
+                k_edge_fix<false><<<grid, kEdgeThreads, 0, s>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
                                                                              p->d_edge_delta, sc != nullptr);
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
         if (sc) {
-            LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, p->child_stream);
-            k_edge_power<<<p->child_n, 32, 0, p->child_stream>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
+            LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, s);
+            k_edge_power<<<p->child_n, 32, 0, s>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
-        CWT_CUDA(p, cudaEventRecord(p->ev_cjoin, p->child_stream));
     }
-    if (p->jobs.empty()) {                       // every row came from the child
-        if (p->child) CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_cjoin, 0));
-        return CWT_OK;
-    }
+    if (p->jobs.empty()) return CWT_OK;          // every row came from the child
 
     // 1. forward transform F(m) = sum_n f(n) e^{+2 pi i m n / M}, m <= M/2
     if (p->fwd_small) {
@@ -815,8 +847,6 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         CWT_CUDA(p, cudaEventRecord(p->ev_join[i - 1], streams[i]));
         CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i - 1], 0));
     }
-
-    if (p->child) CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_cjoin, 0));
 
     // 4. power spectrum: fixed-order reduction of the per-tile partials
     if (spectrum) {

@@ -86,8 +86,6 @@ struct cwt_plan {
     // followed by an edge correction of their 2E outermost outputs
     cwt_plan* child = nullptr;
     int32_t child_r0 = 0, child_n = 0;
-    cudaStream_t child_stream = nullptr;  // the child's work, forked at the start of a call
-    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr;
     int32_t edge_bpr = 0;                 // correction blocks per row
     void* d_edge_rows = nullptr;          // per row: E and the offset of its h table
     float2* d_edge_h = nullptr;           // h(j) = sqrt(w~ dx) psi(w~ j), j in [-E, E]
