@@ -149,13 +149,16 @@ struct EdgeRow { int32_t E; int32_t h_off; };
 constexpr int kEdgeThreads = 256;
 constexpr int64_t kEdgeMax = 4096;           // largest E handled this way
 
-// grid (2 * chunks, rows): block b corrects outputs i in [256 c, 256 c + 256) of
+// grid (2 * chunks, rows): block b corrects outputs i in [64 c, 64 c + 64) of
 // one edge (b even: left, n = i; b odd: right, n = N - E + i), i < E.  With
 // k the term index, the two sums are sliding dot products:
 //   left:  corr(i) = sum_{k=0}^{E-1-i} f(N-1-k) h(i+1+k),
 //   right: corr(i) = sum_{k=0}^{i}     h(-E+k)  f(i-k),
-// taken over tiles of kEdgeKT terms staged in shared memory.  With power,
-// each block records its change of sum |W|^2.
+// taken over tiles of kEdgeKT terms staged in shared memory; the 4 threads of
+// an output take a quarter of each tile and their sums are added in a fixed
+// order.  With power, each block records its change of sum |W|^2.
+constexpr int kEdgeOut = 64;                 // outputs per block
+constexpr int kEdgeSplit = kEdgeThreads / kEdgeOut;
 constexpr int kEdgeKT = 512;
 
 __device__ __forceinline__ float load_f(const void* signal, int f64, int64_t m) {
@@ -166,77 +169,86 @@ template <bool CPLX>
 static __global__ void __launch_bounds__(kEdgeThreads)
     k_edge_fix(const void* __restrict__ signal, int sig_f64, int64_t N, void* W, const float2* __restrict__ h,
                const EdgeRow* __restrict__ rows, double* __restrict__ delta, int do_power) {
-    __shared__ float fs[kEdgeKT + kEdgeThreads];
-    __shared__ float2 hs[kEdgeKT + kEdgeThreads];
+    __shared__ float fs[kEdgeKT + kEdgeOut];
+    __shared__ float2 hs[kEdgeKT + kEdgeOut];
+    __shared__ float2 part[kEdgeSplit][kEdgeOut];
     __shared__ double red[2 * (kEdgeThreads / 32)];
     const int r = blockIdx.y;
     const EdgeRow er = rows[r];
     const int E = er.E;
     const bool left = (blockIdx.x & 1) == 0;
-    const int i0 = (blockIdx.x >> 1) * kEdgeThreads;
-    const int i = i0 + threadIdx.x;
+    const int i0 = (blockIdx.x >> 1) * kEdgeOut;
+    const int o = threadIdx.x % kEdgeOut, q = threadIdx.x / kEdgeOut;
+    const int i = i0 + o;
     const float2* hr = h + er.h_off + E;              // hr[j], j in [-E, E]
     float dpow = 0.f;
     if (i0 < E) {                                     // block-uniform
-        // terms of this block: left k in [0, E - 1 - i0], right k in [0, i0 + 255]
-        const int kmax = left ? E - 1 - i0 : min(i0 + kEdgeThreads - 1, E - 1);
+        // terms of this block: left k in [0, E - 1 - i0], right k in [0, i0 + 63]
+        const int kmax = left ? E - 1 - i0 : min(i0 + kEdgeOut - 1, E - 1);
+        const int klast = left ? E - 1 - i : i;       // this output's last term
         float cr = 0.f, ci = 0.f;
         for (int k0 = 0; k0 <= kmax; k0 += kEdgeKT) {
             __syncthreads();
             if (left) {
-                // fs[kk] = f(N-1-k0-kk), hs[u] = h(i0+1+k0+u), u < KT + 255
+                // fs[kk] = f(N-1-k0-kk), hs[u] = h(i0+1+k0+u), u < KT + 63
                 for (int u = threadIdx.x; u < kEdgeKT; u += kEdgeThreads) {
                     const int k = k0 + u;
                     fs[u] = k <= kmax ? load_f(signal, sig_f64, N - 1 - k) : 0.f;
                 }
-                for (int u = threadIdx.x; u < kEdgeKT + kEdgeThreads; u += kEdgeThreads) {
+                for (int u = threadIdx.x; u < kEdgeKT + kEdgeOut; u += kEdgeThreads) {
                     const int j = i0 + 1 + k0 + u;
                     hs[u] = j <= E ? __ldg(&hr[j]) : make_float2(0.f, 0.f);
                 }
             } else {
-                // hs[kk] = h(-E+k0+kk), fs[u] = f(i0 - k0 - KT + 1 + u), u < KT + 255
+                // hs[kk] = h(-E+k0+kk), fs[u] = f(i0 - k0 - KT + 1 + u), u < KT + 63
                 for (int u = threadIdx.x; u < kEdgeKT; u += kEdgeThreads) {
                     const int k = k0 + u;
                     hs[u] = k <= kmax ? __ldg(&hr[-E + k]) : make_float2(0.f, 0.f);
                 }
-                for (int u = threadIdx.x; u < kEdgeKT + kEdgeThreads; u += kEdgeThreads) {
+                for (int u = threadIdx.x; u < kEdgeKT + kEdgeOut; u += kEdgeThreads) {
                     const int m = i0 - k0 - kEdgeKT + 1 + u;
                     fs[u] = (m >= 0 && m < E) ? load_f(signal, sig_f64, m) : 0.f;
                 }
             }
             __syncthreads();
             if (i < E) {
-                const int kend = min(kEdgeKT, (left ? E - 1 - i : i) - k0 + 1);   // terms of this thread in the tile
-                const int t = threadIdx.x;
+                // this thread's quarter of the tile, clipped to the output's terms
+                const int kb = q * (kEdgeKT / kEdgeSplit);
+                const int ke = min(kb + kEdgeKT / kEdgeSplit, klast - k0 + 1);
 #pragma unroll 8
-                for (int kk = 0; kk < kend; kk++) {
+                for (int kk = kb; kk < ke; kk++) {
                     float fv;
                     float2 hv;
                     if (left) {
                         fv = fs[kk];
-                        hv = hs[t + kk];
+                        hv = hs[o + kk];
                     } else {
                         hv = hs[kk];
-                        fv = fs[t - kk + kEdgeKT - 1];
+                        fv = fs[o - kk + kEdgeKT - 1];
                     }
                     cr = fmaf(hv.x, fv, cr);
                     ci = fmaf(hv.y, fv, ci);
                 }
             }
         }
-        if (i < E) {
+        part[q][o] = make_float2(cr, ci);
+        __syncthreads();
+        if (q == 0 && i < E) {
+            float2 c = part[0][o];
+#pragma unroll
+            for (int u = 1; u < kEdgeSplit; u++) c = make_float2(c.x + part[u][o].x, c.y + part[u][o].y);
             const int64_t n = left ? (int64_t)i : N - E + i;
             if constexpr (CPLX) {
-                float2* q = (float2*)W + (int64_t)r * N + n;
-                const float2 o = *q;
-                const float2 w = make_float2(o.x - cr, o.y - ci);
-                *q = w;
-                dpow = (w.x * w.x + w.y * w.y) - (o.x * o.x + o.y * o.y);
+                float2* w_ = (float2*)W + (int64_t)r * N + n;
+                const float2 ov = *w_;
+                const float2 w = make_float2(ov.x - c.x, ov.y - c.y);
+                *w_ = w;
+                dpow = (w.x * w.x + w.y * w.y) - (ov.x * ov.x + ov.y * ov.y);
             } else {
-                float* q = (float*)W + (int64_t)r * N + n;
-                const float o = *q, w = o - cr;
-                *q = w;
-                dpow = w * w - o * o;
+                float* w_ = (float*)W + (int64_t)r * N + n;
+                const float ov = *w_, w = ov - c.x;
+                *w_ = w;
+                dpow = w * w - ov * ov;
             }
         }
     }
@@ -572,7 +584,7 @@ cwt_status build_plan(cwt_plan* p) {
             }
             emax = std::max(emax, E);
         }
-        p->edge_bpr = (int32_t)(2 * ((emax + kEdgeThreads - 1) / kEdgeThreads));
+        p->edge_bpr = (int32_t)(2 * ((emax + kEdgeOut - 1) / kEdgeOut));
         EdgeRow* d_er = nullptr;
         if ((st = upload(p, &d_er, er)) != CWT_OK) return st;
         p->d_edge_rows = d_er;
@@ -979,7 +991,9 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     // with short wavelet support goes to a periodic N-point child plan
     if (boundary == CWT_BOUNDARY_ZERO && o.fft_len == 0 && is_pow2(N) && N >= 1024 &&
         (wavelet == CWT_WAVELET_GDW || wavelet == CWT_WAVELET_MORLET)) {
-        const int64_t emax = std::min<int64_t>({kEdgeMax, N / 4, M - N});
+        // the correction costs ~E^2 per row against the saving of half an M-point
+        // transform: E <= max(N / 512, 256) (N / 512 measured best at N = 2^20, 2^22)
+        const int64_t emax = std::min<int64_t>({kEdgeMax, std::max<int64_t>(N / 512, 256), N / 4, M - N});
         int r0 = -1, r1 = -1;
         bool contiguous = true;
         for (int32_t i = 0; i < n_scales; i++) {

@@ -244,7 +244,7 @@ def test_graph_replay_matches_direct_launches(env):
 
 
 @pytest.mark.parametrize("N,wavelet,smin,smax,S,order,dtype", [
-    (4096, "gdw", 2.0, 40.0, 9, "asc", "f32"),          # every row short: the padded plan runs no job of its own
+    (4096, "gdw", 2.0, 20.0, 9, "asc", "f32"),          # every row short: the padded plan runs no job of its own
     (1024, "morlet", 4.0, 60.0, 8, "asc", "f32"),       # E up to N/4 = 256, then the padded path
     (1 << 15, "morlet", 4.0, 2e4, 14, "desc", "f32"),   # short rows at the end
     (1 << 15, "gdw", 2.0, 2e4, 13, "shuffled", "f32"),  # short rows not contiguous: all padded
