@@ -344,6 +344,8 @@ void free_plan(cwt_plan* p) {
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_pre) cudaEventDestroy(p->ev_pre);
+    if (p->ev_pfwd) cudaEventDestroy(p->ev_pfwd);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Zt, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
@@ -595,6 +597,10 @@ cwt_status build_plan(cwt_plan* p) {
     // side streams and events, and the shared-memory opt-in of every kernel the
     // plan launches, are set up here so that no call made while capturing needs them
     CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    if (p->child) {
+        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_pre, cudaEventDisableTiming));
+        CWT_CUDA(p, cudaEventCreateWithFlags(&p->ev_pfwd, cudaEventDisableTiming));
+    }
 
     for (int i = 0; i < cwt_plan::kSide; i++) {
         CWT_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
@@ -723,63 +729,73 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     P.W = W;
     P.do_power = spectrum != nullptr;
 
-    // rows with short wavelet support: the periodic child plan (with its own
-    // side streams) and the edge correction, first on the call's stream; running
-    // it beside this plan's streams put too many intermediates in flight for L2
-    if (p->child) {
-        const size_t esz = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
-        void* Wc = (char*)W + (size_t)p->child_r0 * (size_t)p->N * esz;
-        double* sc = spectrum ? spectrum + p->child_r0 : nullptr;
-        if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
+    // rows with short wavelet support: a periodic N-point child plan (with its
+    // own side streams) on the call's stream, then the edge correction of those
+    // rows.  This plan's forward transform runs beside the child on a side
+    // stream, and the edge correction beside this plan's own work.
+    const size_t esz = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
+    void* Wc = p->child ? (char*)W + (size_t)p->child_r0 * (size_t)p->N * esz : nullptr;
+    double* sc = (p->child && spectrum) ? spectrum + p->child_r0 : nullptr;
+    auto edge_fix = [&](cudaStream_t es) -> cwt_status {
         {
-            LaunchTimer lt(p, CWT_KCLASS_BAND, 0.0, s);
+            LaunchTimer lt(p, CWT_KCLASS_BAND, 0.0, es);
             const dim3 grid((unsigned)p->edge_bpr, (unsigned)p->child_n);
             const EdgeRow* rows = (const EdgeRow*)p->d_edge_rows;
             const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
             if (p->wavelet == CWT_WAVELET_MORLET)
-                k_edge_fix<true><<<grid, kEdgeThreads, 0, s>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
-                                                                            p->d_edge_delta, sc != nullptr);
+                k_edge_fix<true><<<grid, kEdgeThreads, 0, es>>>(signal, f64, p->N, Wc, p->d_edge_h, rows, p->d_edge_delta,
+                                                                sc != nullptr);
             else
-                k_edge_fix<false><<<grid, kEdgeThreads, 0, s>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
-                                                                             p->d_edge_delta, sc != nullptr);
+                k_edge_fix<false><<<grid, kEdgeThreads, 0, es>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
+                                                                 p->d_edge_delta, sc != nullptr);
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
         if (sc) {
-            LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, s);
-            k_edge_power<<<p->child_n, 32, 0, s>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
+            LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, es);
+            k_edge_power<<<p->child_n, 32, 0, es>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
             CWT_CUDA(p, cudaGetLastError());
             lt.done();
         }
+        return CWT_OK;
+    };
+    if (p->jobs.empty()) {                       // every row comes from the child
+        if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
+        return edge_fix(s);
     }
-    if (p->jobs.empty()) return CWT_OK;          // every row came from the child
+    cudaStream_t fs = s;                         // stream of this plan's forward transform
+    if (p->child) {
+        CWT_CUDA(p, cudaEventRecord(p->ev_pre, s));
+        CWT_CUDA(p, cudaStreamWaitEvent(p->side[0], p->ev_pre, 0));
+        fs = p->side[0];
+    }
 
     // 1. forward transform F(m) = sum_n f(n) e^{+2 pi i m n / M}, m <= M/2
     if (p->fwd_small) {
         const Entry& e = tb.fwd_small[p->logM];
         Params Q = P;
         Q.A = 1;
-        if ((st = launch(p, e, dim3(1), stage_smem(p->logM, 1), Q, s, CWT_KCLASS_FORWARD,
+        if ((st = launch(p, e, dim3(1), stage_smem(p->logM, 1), Q, fs, CWT_KCLASS_FORWARD,
                          p->fwd_in_bytes + p->fwd_out_bytes)) != CWT_OK)
             return st;
     } else {
         const Entry& e1 = tb.fwd1[p->wide_loga];
         const int L = 1 << p->wide_logl;
-        if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga, e1.T), P, s,
+        if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga, e1.T), P, fs,
                          CWT_KCLASS_FORWARD, p->fwd_in_bytes)) != CWT_OK)
             return st;
         const Entry& e2 = tb.fwd2[p->wide_logl];
         Params Q = P;
         Q.A = (int32_t)(p->M >> p->wide_logl);
-        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, s,
+        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, fs,
                          CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
             return st;
     }
 
     // the band jobs' values Z(k), once per call (each band CTA reads its job's table)
     if (p->n_band_jobs > 0) {
-        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
-        k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, s>>>(P);
+        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, fs);
+        k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, fs>>>(P);
         CWT_CUDA(p, cudaGetLastError());
         lt.done();
     }
@@ -788,10 +804,16 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     if (!p->wide.empty()) {
         const int L = 1 << p->wide_logl;
         const int A = (int)(p->M >> p->wide_logl);
-        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
-        k_spec_transpose<<<dim3((L + 31) / 32, (A + 31) / 32), dim3(32, 8), 0, s>>>(p->d_Fp, p->d_Ft, (int)p->M, L, A);
+        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, fs);
+        k_spec_transpose<<<dim3((L + 31) / 32, (A + 31) / 32), dim3(32, 8), 0, fs>>>(p->d_Fp, p->d_Ft, (int)p->M, L, A);
         CWT_CUDA(p, cudaGetLastError());
         lt.done();
+    }
+
+    if (p->child) {
+        CWT_CUDA(p, cudaEventRecord(p->ev_pfwd, fs));
+        if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
+        CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_pfwd, 0));
     }
 
     // 2-3. band scales (one launch per DFT length) and wide-scale batches
@@ -809,6 +831,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             CWT_CUDA(p, cudaStreamWaitEvent(streams[i], p->ev_fork, 0));
         }
     }
+    if (p->child && (st = edge_fix(streams[nstreams - 1])) != CWT_OK) return st;
     int next = 0;
     // wide batches first (longest chains), round robin; band groups fill in
     for (size_t wi = 0; wi < p->wide.size(); wi++) {

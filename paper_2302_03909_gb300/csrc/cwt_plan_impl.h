@@ -86,6 +86,7 @@ struct cwt_plan {
     // followed by an edge correction of their 2E outermost outputs
     cwt_plan* child = nullptr;
     int32_t child_r0 = 0, child_n = 0;
+    cudaEvent_t ev_pre = nullptr, ev_pfwd = nullptr;   // this plan's forward beside the child
     int32_t edge_bpr = 0;                 // correction blocks per row
     void* d_edge_rows = nullptr;          // per row: E and the offset of its h table
     float2* d_edge_h = nullptr;           // h(j) = sqrt(w~ dx) psi(w~ j), j in [-E, E]
