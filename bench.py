@@ -50,6 +50,12 @@ def parse_args():
                     help="run one boundary of the workload only")
     ap.add_argument("--scale-range", type=int, nargs=2, metavar=("I", "J"),
                     help="keep the workload's scales I..J-1 only (ascending dilation)")
+    # serving: a Poisson trace of requests through paper_2302_03909_gb300.serving
+    ap.add_argument("--serving", action="store_true", help="measure request latency instead of throughput")
+    ap.add_argument("--rate", type=float, default=500.0, help="serving: requests per second")
+    ap.add_argument("--seconds", type=float, default=5.0, help="serving: length of the arrival trace")
+    ap.add_argument("--slots", type=int, default=4, help="serving: requests in flight at once")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
     return ap.parse_args()
 
 
@@ -238,6 +244,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Poisson arrivals (N = 2^10..2^24, 16..128 scales, GDW or Morlet, periodic or
+    zero boundary) served with ``--slots`` streams, then the same trace with one
+    slot (serial execution); plans of every request shape are created first
+    (a resident plan cache).  Prints one JSON line of latency percentiles."""
+    import torch
+
+    from paper_2302_03909_gb300 import serving
+
+    torch.cuda.set_device(0)
+    trace = serving.poisson_trace(args.rate, args.seconds)
+    pool = {}
+    for r in trace:
+        if r.N not in pool:
+            pool[r.N] = torch.tensor(synth.lognormal_field(r.N, seed=synth.BASE_SEED + 50 + r.N.bit_length()),
+                                     dtype=torch.float32).pin_memory()
+        r.signal = pool[r.N]
+    budget = int(args.budget_gb * (1 << 30))
+    out = {}
+    for label, slots in (("concurrent", args.slots), ("serial", 1)):
+        for r in trace:
+            r.t_admit = r.t_done = float("nan")
+        srv = serving.Server(budget, slots=slots, plan_cache_bytes=budget // 2)
+        keys = sorted({r.key for r in trace})
+        for k in keys:                                       # resident plans
+            srv.cache.release(k, srv.cache.acquire(k))
+        srv.cache.hits = srv.cache.misses = 0
+        # one untimed pass over the shapes (first-use costs), then the timed trace
+        warm = [serving.Request(i, *k, 0.0, signal=pool[k[0]]) for i, k in enumerate(keys)]
+        serving.run_trace(srv, warm)
+        srv.completed.clear()
+        torch.cuda.synchronize()
+        out[label] = serving.run_trace(srv, [dataclasses_replace(r) for r in trace])
+        srv.close()
+    mean_units = float(np.mean([len(r.scales) * r.N for r in trace]))
+    line = {"impl": "ours", "metric": "CWT serving latency", "unit": "ms", "higher_is_better": False,
+            "p50_ms": out["concurrent"]["p50_ms"], "p99_ms": out["concurrent"]["p99_ms"],
+            "serial_p50_ms": out["serial"]["p50_ms"], "serial_p99_ms": out["serial"]["p99_ms"],
+            "offered_scale_samples_per_s": mean_units * len(trace) / args.seconds,
+            "concurrent": out["concurrent"], "serial": out["serial"],
+            "config": {"rate_per_s": args.rate, "seconds": args.seconds, "requests": len(trace),
+                       "slots": args.slots, "budget_gb": args.budget_gb, "N": "2^10..2^24 (powers of two)",
+                       "n_scales": "16..128", "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],
+                       "plans": "resident, created before the trace"},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
+def dataclasses_replace(r):
+    import dataclasses
+    return dataclasses.replace(r)
+
+
 def run_ours(args):
     import torch
 
@@ -385,6 +444,9 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    if args.serving and args.impl == "ours":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -906,6 +906,14 @@ cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaS
         CWT_CUDA(p, cudaGraphLaunch(p->gexec, s));
         return CWT_OK;
     }
+    // capture only when a call repeats the previous call's pointers: a caller
+    // with fresh buffers every call (a request server) launches directly
+    if (p->skey[0] != signal || p->skey[1] != W || p->skey[2] != spectrum) {
+        p->skey[0] = signal;
+        p->skey[1] = W;
+        p->skey[2] = spectrum;
+        return run_launches(p, signal, W, spectrum, s);
+    }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();

@@ -69,6 +69,7 @@ struct cwt_plan {
     // captured launch sequence, replayed while the call's pointers repeat
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[3] = {};
+    const void* skey[3] = {};             // pointers of the last direct call
     bool graphs_ok = true;
 
     // timing hook (cwt_plan_set_timing)

@@ -1,0 +1,278 @@
+"""Serving loop for CWT requests on one GPU.
+
+Requests (a signal, its scales, a wavelet and a boundary) arrive over time.
+The loop has three parts:
+
+* ``Admission``: a FIFO queue admitted against a device-memory budget.  A
+  request needs its signal, its W and its spectrum, plus the workspace of a
+  plan instance when none is idle.  Requests are admitted in arrival order:
+  the head of the queue waits for memory and for a free slot, and nothing
+  overtakes it.  A request larger than the whole budget is rejected at
+  submission.
+* ``PlanCache``: plans resident on the device, keyed by request shape.  A
+  plan instance runs on one stream at a time (its workspace is shared), so a
+  key can have several instances.  Idle instances are evicted
+  least-recently-used once the cache exceeds its byte budget.
+* ``Server``: ``slots`` CUDA streams.  An admitted request takes a free slot
+  and a plan instance, copies its signal to the device, runs
+  ``cwt_exec_with_power`` and records an event; completions are found by
+  polling the events, and free their memory and slot.
+
+``run_trace`` replays a timed arrival trace (open loop) and reports latency
+percentiles; ``poisson_trace`` draws the arrivals.  Both the admission and
+the cache are plain host logic, tested on CPU with fakes.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, Dict, List, Optional, Tuple
+
+import numpy as np
+
+_WBYTES = {"morlet": 8, "gdw": 4, "mexhat": 4, "cbsw": 4, "cwgdw": 4}
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    N: int
+    scales: Tuple[float, ...]
+    wavelet: str
+    boundary: str
+    t_arrival: float
+    signal: object = None           # host float32 array / pinned CPU tensor of N samples
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    W: object = None                # device result, kept when the server is asked to
+    spectrum: object = None
+
+    @property
+    def key(self):
+        return (self.N, self.scales, self.wavelet, self.boundary)
+
+    @property
+    def io_bytes(self) -> int:
+        """Device bytes of the request's own buffers: signal, W and spectrum."""
+        S = len(self.scales)
+        return self.N * 4 + S * self.N * _WBYTES[self.wavelet] + S * 8
+
+
+class PlanCache:
+    """Plan instances by key.  ``acquire`` lends an idle instance (or makes
+    one with ``factory``); ``release`` returns it.  Idle instances are
+    evicted least-recently-used while the cache holds more than
+    ``max_bytes`` of plan workspace."""
+
+    def __init__(self, factory: Callable, max_bytes: int, size_of: Callable = lambda p: p.workspace_bytes,
+                 close: Callable = lambda p: p.close()):
+        self.factory, self.max_bytes, self.size_of, self.close = factory, max_bytes, size_of, close
+        self.idle: "collections.OrderedDict[tuple, List]" = collections.OrderedDict()
+        self.busy = 0
+        self.bytes = 0
+        self.hits = self.misses = self.evictions = 0
+
+    def has_idle(self, key) -> bool:
+        return bool(self.idle.get(key))
+
+    def acquire(self, key):
+        lst = self.idle.get(key)
+        if lst:
+            self.hits += 1
+            p = lst.pop()
+            if not lst:
+                del self.idle[key]
+        else:
+            self.misses += 1
+            p = self.factory(key)
+            self.bytes += self.size_of(p)
+            self.trim()
+        self.busy += 1
+        return p
+
+    def release(self, key, p):
+        self.busy -= 1
+        self.idle.setdefault(key, []).append(p)
+        self.idle.move_to_end(key)
+        self.trim()
+
+    def trim(self):
+        while self.bytes > self.max_bytes and self.idle:
+            key, lst = next(iter(self.idle.items()))
+            p = lst.pop(0)
+            if not lst:
+                del self.idle[key]
+            self.bytes -= self.size_of(p)
+            self.close(p)
+            self.evictions += 1
+
+    def clear(self):
+        for lst in self.idle.values():
+            for p in lst:
+                self.close(p)
+        self.idle.clear()
+        self.bytes = 0
+
+
+class Admission:
+    """FIFO admission against a byte budget and a number of slots."""
+
+    def __init__(self, budget_bytes: int, slots: int):
+        self.budget, self.slots = budget_bytes, slots
+        self.queue: "collections.deque[Request]" = collections.deque()
+        self.in_flight_bytes = 0
+        self.free_slots = list(range(slots))[::-1]
+
+    def submit(self, req: Request, extra_bytes: int = 0):
+        if req.io_bytes + extra_bytes > self.budget:
+            raise ValueError(f"request {req.rid} needs {req.io_bytes + extra_bytes} bytes, "
+                             f"over the {self.budget}-byte budget")
+        self.queue.append(req)
+
+    def next_admissible(self, need: Callable[[Request], int]) -> Optional[Tuple[Request, int, int]]:
+        """Pops the queue head if a slot is free and its bytes fit: (request, slot, bytes)."""
+        if not self.queue or not self.free_slots:
+            return None
+        req = self.queue[0]
+        b = need(req)
+        if self.in_flight_bytes + b > self.budget:
+            return None
+        self.queue.popleft()
+        self.in_flight_bytes += b
+        return req, self.free_slots.pop(), b
+
+    def done(self, slot: int, nbytes: int):
+        self.in_flight_bytes -= nbytes
+        self.free_slots.append(slot)
+
+
+class Server:
+    """Runs admitted requests on ``slots`` CUDA streams of one device."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4, plan_cache_bytes: Optional[int] = None,
+                 keep_results: bool = False, device: int = 0):
+        import torch
+
+        import paper_2302_03909_gb300 as cwt
+        self.torch, self.cwt = torch, cwt
+        self.dev = torch.device("cuda", device)
+        self.adm = Admission(budget_bytes, slots)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.cache = PlanCache(self._make_plan, plan_cache_bytes if plan_cache_bytes is not None
+                               else budget_bytes // 4)
+        self.keep = keep_results
+        self.in_flight: List[tuple] = []      # (req, slot, bytes, plan, event, tensors)
+        self.completed: List[Request] = []
+        self._ws_guess: Dict[tuple, int] = {}
+
+    def _make_plan(self, key):
+        N, scales, wavelet, boundary = key
+        p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary)
+        self._ws_guess[key] = p.workspace_bytes
+        return p
+
+    def _need(self, req: Request) -> int:
+        # a new instance's workspace counts against the budget while it is busy
+        extra = 0 if self.cache.has_idle(req.key) else self._ws_guess.get(req.key, 0)
+        return req.io_bytes + extra
+
+    def submit(self, req: Request):
+        self.adm.submit(req)
+
+    def _launch(self, req: Request, slot: int, nbytes: int, now: float):
+        torch = self.torch
+        st = self.streams[slot]
+        plan = self.cache.acquire(req.key)
+        with torch.cuda.stream(st):
+            sig = torch.empty(req.N, dtype=torch.float32, device=self.dev)
+            sig.copy_(req.signal, non_blocking=True)
+            W = plan.empty_output(self.dev)
+            sp = torch.empty(plan.n_scales, dtype=torch.float64, device=self.dev)
+            self.cwt.cwt_exec_with_power(plan, sig, W, sp, st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        req.t_admit = now
+        self.in_flight.append((req, slot, nbytes, plan, ev, (sig, W, sp)))
+
+    def poll(self, now: float) -> int:
+        """Retires finished requests and admits queued ones; returns the number retired."""
+        n = 0
+        still = []
+        for item in self.in_flight:
+            req, slot, nbytes, plan, ev, (sig, W, sp) = item
+            if ev.query():
+                req.t_done = now
+                if self.keep:
+                    req.W, req.spectrum = W, sp
+                self.cache.release(req.key, plan)
+                self.adm.done(slot, nbytes)
+                self.completed.append(req)
+                n += 1
+            else:
+                still.append(item)
+        self.in_flight = still
+        while True:
+            nxt = self.adm.next_admissible(self._need)
+            if nxt is None:
+                break
+            self._launch(*nxt, now)
+        return n
+
+    def idle(self) -> bool:
+        return not self.in_flight and not self.adm.queue
+
+    def close(self):
+        self.torch.cuda.synchronize(self.dev)
+        self.cache.clear()
+
+
+def run_trace(server: Server, trace: List[Request], max_seconds: float = 600.0) -> dict:
+    """Replays the arrivals of ``trace`` (t_arrival in seconds from the start)
+    in real time and returns latency statistics (milliseconds)."""
+    trace = sorted(trace, key=lambda r: r.t_arrival)
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(trace) or not server.idle():
+        now = time.perf_counter() - t0
+        if now > max_seconds:
+            raise TimeoutError("trace did not drain in time")
+        while i < len(trace) and trace[i].t_arrival <= now:
+            server.submit(trace[i])
+            i += 1
+        server.poll(now)
+        if i < len(trace) and server.idle():
+            time.sleep(max(0.0, min(trace[i].t_arrival - now, 1e-3)))
+    wall = time.perf_counter() - t0
+    lat = np.array([(r.t_done - r.t_arrival) * 1e3 for r in server.completed])
+    units = sum(len(r.scales) * r.N for r in server.completed)
+    return {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "wall_s": wall, "scale_samples_per_s": units / wall,
+            "plan_hits": server.cache.hits, "plan_misses": server.cache.misses,
+            "plan_evictions": server.cache.evictions}
+
+
+def poisson_trace(rate: float, seconds: float, seed: int = 20230213, log2n=(10, 24), n_scales=(16, 128),
+                  shapes_per_log2n: int = 4) -> List[Request]:
+    """Poisson arrivals at ``rate`` per second for ``seconds``.  Each request:
+    N = 2^u with u uniform over log2n (power-of-two lengths, so both
+    boundaries apply), a scale count drawn from ``shapes_per_log2n`` values
+    spread over n_scales (requests of one service repeat shapes, which the
+    plan cache exploits), log-spaced dilations from 4 to N/4, the GDW or the
+    Morlet and the periodic or zero boundary with equal odds."""
+    rng = np.random.default_rng(seed)
+    t, out, rid = 0.0, [], 0
+    counts = np.unique(np.linspace(n_scales[0], n_scales[1], shapes_per_log2n).astype(int))
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        u = int(rng.integers(log2n[0], log2n[1] + 1))
+        N = 1 << u
+        S = int(rng.choice(counts))
+        sc = tuple(float(x) for x in np.exp(np.linspace(np.log(4.0), np.log(max(8.0, N / 4)), S)))
+        out.append(Request(rid, N, sc, "gdw" if rng.random() < 0.5 else "morlet",
+                           "periodic" if rng.random() < 0.5 else "zero", t))
+        rid += 1
+    return out

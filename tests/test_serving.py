@@ -1,0 +1,90 @@
+"""Host logic of the request server (paper_2302_03909_gb300.serving): the plan
+cache and the FIFO admission, with fakes in place of the GPU; the arrival
+trace generator."""
+import numpy as np
+import pytest
+
+from paper_2302_03909_gb300 import serving
+
+
+class FakePlan:
+    def __init__(self, key, nbytes):
+        self.key, self.workspace_bytes, self.closed = key, nbytes, False
+
+    def close(self):
+        self.closed = True
+
+
+def test_plan_cache_reuses_idle_instances_and_evicts_lru():
+    made = []
+
+    def factory(key):
+        p = FakePlan(key, 100)
+        made.append(p)
+        return p
+
+    c = serving.PlanCache(factory, max_bytes=250)
+    a = c.acquire("a")
+    a2 = c.acquire("a")                    # busy instance: a second one is made
+    assert a is not a2 and c.misses == 2 and c.busy == 2
+    c.release("a", a)
+    assert c.acquire("a") is a and c.hits == 1
+    c.release("a", a)
+    c.release("a", a2)
+    b = c.acquire("b")                     # 300 bytes > 250: an idle "a" goes
+    assert c.evictions == 1 and c.bytes == 200 and sum(p.closed for p in made) == 1
+    assert not b.closed                    # busy instances are never evicted
+    c.release("b", b)
+    c.clear()
+    assert all(p.closed for p in made) and c.bytes == 0
+
+
+def req(rid, N=1024, S=4, wavelet="morlet", t=0.0):
+    return serving.Request(rid, N, tuple(np.linspace(2, 10, S)), wavelet, "periodic", t)
+
+
+def test_admission_fifo_budget_and_slots():
+    r = [req(i) for i in range(5)]
+    nb = r[0].io_bytes
+    adm = serving.Admission(budget_bytes=3 * nb, slots=2)
+    for x in r:
+        adm.submit(x)
+    got = []
+    while True:
+        nxt = adm.next_admissible(lambda q: q.io_bytes)
+        if nxt is None:
+            break
+        got.append(nxt)
+    assert [g[0].rid for g in got] == [0, 1]          # two slots
+    adm.done(got[0][1], got[0][2])
+    nxt = adm.next_admissible(lambda q: q.io_bytes)
+    assert nxt[0].rid == 2                             # arrival order
+    big = req(9, N=1 << 20, S=128)
+    with pytest.raises(ValueError):
+        serving.Admission(budget_bytes=nb, slots=1).submit(big)
+
+
+def test_admission_head_of_line_waits_for_memory():
+    small, large = req(0), req(1, N=1 << 14, S=16)
+    adm = serving.Admission(budget_bytes=large.io_bytes + small.io_bytes // 2, slots=4)
+    adm.submit(small)
+    adm.submit(large)
+    adm.submit(req(2))
+    a = adm.next_admissible(lambda q: q.io_bytes)
+    assert a[0].rid == 0
+    assert adm.next_admissible(lambda q: q.io_bytes) is None     # large waits, small behind it too
+    adm.done(a[1], a[2])
+    assert adm.next_admissible(lambda q: q.io_bytes)[0].rid == 1
+    assert adm.in_flight_bytes == large.io_bytes
+
+
+def test_poisson_trace_shape():
+    tr = serving.poisson_trace(400.0, 2.0, seed=3)
+    assert 650 < len(tr) < 950                          # ~800 arrivals
+    t = np.array([r.t_arrival for r in tr])
+    assert np.all(np.diff(t) > 0) and t[-1] <= 2.0
+    assert {r.N for r in tr} <= {1 << u for u in range(10, 25)}
+    assert all(16 <= len(r.scales) <= 128 for r in tr)
+    assert {r.wavelet for r in tr} == {"gdw", "morlet"} and {r.boundary for r in tr} == {"periodic", "zero"}
+    tr2 = serving.poisson_trace(400.0, 2.0, seed=3)
+    assert [(r.N, r.key) for r in tr] == [(r.N, r.key) for r in tr2]
