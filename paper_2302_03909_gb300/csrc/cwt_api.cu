@@ -289,6 +289,18 @@ void psi_x(int wavelet, double omega0, double x, double* re, double* im) {
 
 }  // namespace
 
+// Periodic boundary with N not a power of two: ext[m] = f((m - E) mod N),
+// m < N + 2E, the signal extended periodically by E samples on each side.
+static __global__ void k_periodic_extend(const void* __restrict__ f, int f64, int64_t N, int64_t E,
+                                         void* __restrict__ ext) {
+    const int64_t total = N + 2 * E;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < total; m += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = ((m - E) % N + N) % N;
+        if (f64) ((double*)ext)[m] = __ldg(&((const double*)f)[src]);
+        else ((float*)ext)[m] = __ldg(&((const float*)f)[src]);
+    }
+}
+
 // ====================================================================== plan
 
 
@@ -356,6 +368,8 @@ void free_plan(cwt_plan* p) {
     for (void* q : edge)
         if (q) cudaFree(q);
     if (p->child) free_plan(p->child);
+    for (cwt_plan* q : p->subs) free_plan(q);
+    if (p->d_ext) cudaFree(p->d_ext);
     delete p;
 }
 
@@ -640,6 +654,8 @@ Params base_params(const cwt_plan* p) {
     P.jobs = p->d_jobs;
     P.tile_job = p->d_tile_job;
     P.N = p->N;
+    P.out_off = p->out_off;
+    P.out_len = p->out_len;
     P.M = (int32_t)p->M;
     P.h = p->h;
     P.wavelet = p->wavelet;
@@ -724,6 +740,26 @@ cwt_status check_device(cwt_plan* p) {
 cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     const Tables& tb = tables();
     cwt_status st;
+    if (!p->subs.empty()) {                      // periodic, N not a power of two
+        const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
+        const size_t se = f64 ? sizeof(double) : sizeof(float);
+        const size_t we = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
+        {
+            LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
+            const int64_t total = p->N + 2 * p->ext_E;
+            const unsigned blocks = (unsigned)std::min<int64_t>(4096, (total + 255) / 256);
+            k_periodic_extend<<<blocks, 256, 0, s>>>(signal, f64, p->N, p->ext_E, p->d_ext);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
+        for (size_t i = 0; i < p->subs.size(); i++) {
+            const void* sig = (const char*)p->d_ext + (size_t)(p->ext_E - p->sub_E[i]) * se;
+            void* Wi = (char*)W + (size_t)p->sub_r0[i] * (size_t)p->N * we;
+            double* spi = spectrum ? spectrum + p->sub_r0[i] : nullptr;
+            if ((st = run_launches(p->subs[i], sig, Wi, spi, s)) != CWT_OK) return st;
+        }
+        return CWT_OK;
+    }
     Params P = base_params(p);
     P.signal = signal;
     P.W = W;
@@ -886,7 +922,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     // 4. power spectrum: fixed-order reduction of the per-tile partials
     if (spectrum) {
         LaunchTimer lt(p, CWT_KCLASS_POWER, 8.0 * (double)(p->n_partials + p->S), s);
-        k_power_finalize<<<p->S, 32, 0, s>>>(p->d_partials, p->d_part_off, p->d_part_cnt, p->S, p->N, spectrum);
+        k_power_finalize<<<p->S, 32, 0, s>>>(p->d_partials, p->d_part_off, p->d_part_cnt, p->S, p->out_len, spectrum);
         CWT_CUDA(p, cudaGetLastError());
         lt.done();
     }
@@ -946,6 +982,79 @@ bool aligned(const void* q, size_t a) { return ((uintptr_t)q % a) == 0; }
 cwt_status plan_fail(cwt_plan* p, cwt_status st, const char* msg) { return fail(p, st, msg); }
 cwt_status plan_check_device(cwt_plan* p) { return check_device(p); }
 
+// Periodic boundary with N not a power of two (GDW, Morlet).  A scale whose
+// wavelet is negligible beyond E samples gives the same W on [0, N) as the
+// zero-boundary transform of the signal extended periodically by E samples on
+// each side, kept on [E, E + N), when the padded length is at least N + 3E
+// (the window sees no wrap-around).  Consecutive rows sharing the power-of-two
+// length M >= N + 3E form one zero-boundary sub-plan of fft_len M.  Scales
+// whose spectrum is not negligible (1e-7 of its peak) at the Nyquist frequency
+// are refused: their band-limited wavelet rings instead of decaying.
+cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales,
+                                    int32_t wavelet, const cwt_plan_opts& o) {
+    if (wavelet != CWT_WAVELET_GDW && wavelet != CWT_WAVELET_MORLET) return CWT_ERR_UNSUPPORTED;
+    std::vector<double> wt(n_scales);
+    for (int32_t i = 0; i < n_scales; i++) wt[i] = o.scale_unit == CWT_SCALE_DILATION ? 1.0 / scales[i] : scales[i];
+    double u_lo, u_hi;
+    wavelet_band(wavelet, o.omega0, 1e-7, &u_lo, &u_hi);
+    std::vector<int64_t> E(n_scales), Mr(n_scales);
+    for (int32_t i = 0; i < n_scales; i++) {
+        const double nyq = kPi / wt[i];                  // u at the Nyquist frequency
+        if (u_hi >= nyq || u_lo <= -nyq) return CWT_ERR_UNSUPPORTED;
+        E[i] = edge_width(wavelet, wt[i]);
+        Mr[i] = int64_t(1) << ilog2(N + 3 * E[i]);
+        if (Mr[i] < N + 3 * E[i]) Mr[i] <<= 1;
+        if (Mr[i] > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
+    }
+    cwt_plan* p = new (std::nothrow) cwt_plan();
+    if (!p) return CWT_ERR_OOM;
+    p->N = N;
+    p->out_len = N;
+    p->S = n_scales;
+    p->wavelet = wavelet;
+    p->boundary = CWT_BOUNDARY_PERIODIC;
+    p->opts = o;
+    p->w_tilde = wt;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        free_plan(p);
+        return CWT_ERR_CUDA;
+    }
+    for (int32_t r0 = 0; r0 < n_scales;) {
+        int32_t r1 = r0 + 1;
+        while (r1 < n_scales && Mr[r1] == Mr[r0]) r1++;
+        int64_t Eg = 0;
+        for (int32_t i = r0; i < r1; i++) Eg = std::max(Eg, E[i]);
+        cwt_plan_opts so = o;
+        so.scale_unit = CWT_SCALE_W_TILDE;
+        so.fft_len = Mr[r0];
+        cwt_plan* sub = nullptr;
+        cwt_status st = cwt_plan_create_ex(&sub, N + 2 * Eg, wt.data() + r0, r1 - r0, wavelet, CWT_BOUNDARY_ZERO, &so);
+        if (st != CWT_OK) {
+            free_plan(p);
+            return st;
+        }
+        sub->out_off = Eg;
+        sub->out_len = N;
+        p->subs.push_back(sub);
+        p->sub_r0.push_back(r0);
+        p->sub_E.push_back(Eg);
+        p->ext_E = std::max(p->ext_E, Eg);
+        p->ws_bytes += sub->ws_bytes;
+        p->M = std::max(p->M, Mr[r0]);
+        r0 = r1;
+    }
+    p->logM = ilog2(p->M);
+    const size_t se = o.input_dtype == CWT_INPUT_F64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaMalloc(&p->d_ext, (size_t)(N + 2 * p->ext_E) * se);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : CWT_ERR_CUDA;
+    }
+    p->ws_bytes += (size_t)(N + 2 * p->ext_E) * se;
+    *plan = p;
+    return CWT_OK;
+}
+
 // ====================================================================== ABI
 
 extern "C" {
@@ -989,7 +1098,7 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     int64_t M;
     if (boundary == CWT_BOUNDARY_PERIODIC) {
         if (o.fft_len != 0 && o.fft_len != N) return CWT_ERR_INVALID_ARG;
-        if (!is_pow2(N)) return CWT_ERR_UNSUPPORTED;
+        if (!is_pow2(N)) return create_periodic_extended(plan, N, scales, n_scales, wavelet, o);
         M = N;
     } else {
         if (o.fft_len != 0) {
@@ -1005,6 +1114,7 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     cwt_plan* p = new (std::nothrow) cwt_plan();
     if (!p) return CWT_ERR_OOM;
     p->N = N;
+    p->out_len = N;
     p->M = M;
     p->logM = ilog2(M);
     p->S = n_scales;
@@ -1176,6 +1286,7 @@ cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable) {
     release_events(plan);
     plan->timing = enable != 0;
     if (plan->child) cwt_plan_set_timing(plan->child, enable);
+    for (cwt_plan* q : plan->subs) cwt_plan_set_timing(q, enable);
     for (int c = 0; c < CWT_KCLASS_COUNT; c++) {
         plan->t_ms[c] = 0.0;
         plan->t_launches[c] = 0;
@@ -1198,9 +1309,16 @@ cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t cls, double* total_ms, in
     release_events(plan);
     double cm = 0.0, cb = 0.0;
     int64_t cn = 0;
-    if (plan->child) {
-        cwt_status st = cwt_plan_get_timing(plan->child, cls, &cm, &cn, &cb);
+    std::vector<cwt_plan*> kids(plan->subs);
+    if (plan->child) kids.push_back(plan->child);
+    for (cwt_plan* q : kids) {
+        double m = 0.0, b = 0.0;
+        int64_t n = 0;
+        cwt_status st = cwt_plan_get_timing(q, cls, &m, &n, &b);
         if (st != CWT_OK) return st;
+        cm += m;
+        cn += n;
+        cb += b;
     }
     if (total_ms) *total_ms = plan->t_ms[cls] + cm;
     if (launches) *launches = plan->t_launches[cls] + cn;

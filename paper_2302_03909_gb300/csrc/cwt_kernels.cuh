@@ -73,6 +73,7 @@ struct Params {
     const Job* jobs;
     const int32_t* tile_job; // band launches: tile -> job
     int64_t N;
+    int64_t out_off, out_len; // W rows keep outputs n in [out_off, out_off + out_len), row stride out_len
     int32_t M, h;            // M = 2^logM, two-level table split h
     int32_t A;               // number of columns d (= M / L)
     int32_t job0;            // wide launches: job = job0 + blockIdx.y
@@ -399,9 +400,6 @@ __device__ __forceinline__ void block_sum2(float a, float b, double* out_a, doub
 
 // ------------------------------------------------------- output to W rows
 
-// Stores X(d + A c) for the last stage's outputs c = j + r * cstride
-// (d = d0 + t); with CROP, outputs n >= N (zero-boundary padding) are
-// dropped.  Accumulates |W|^2 per row.
 // Cache policy of the two large streams.  W is written once and never read
 // back here: its stores are cache-streaming (evict-first).  The wide-scale
 // intermediate Y is stored with an L2 evict-last policy by pass 1, so that it
@@ -419,6 +417,10 @@ __device__ __forceinline__ void st_keep(float2* q, float2 v, uint64_t pol) {
 }
 __device__ __forceinline__ float2 ld_once(const float2* q) { return __ldcs(q); }
 
+// Stores X(d + A c) for the last stage's outputs c = j + r * cstride
+// (d = d0 + t) at W[row][n - out_off]; with CROP, only outputs n in
+// [out_off, out_off + out_len) are kept (the zero-boundary crop, or the
+// window of a periodically extended signal).  Accumulates |W|^2 per row.
 template <bool CROP>
 struct WOut {
     const Params* p;
@@ -431,23 +433,24 @@ struct WOut {
     __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int cstride) {
         const int n0 = d0 + t + p->A * j;
         const int step = p->A * cstride;
-        const int N = (int)p->N;
+        const int off = (int)p->out_off;
+        const unsigned len = (unsigned)p->out_len;
         if (rc) {
-            float2* q = rc + n0;
+            float2* q = rc + (n0 - off);
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (!CROP || n0 + r * step < N) {
+                if (!CROP || (unsigned)(n0 + r * step - off) < len) {
                     st_stream(q + r * step, v[r]);
                     pw0 = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, pw0));
                 }
             }
         } else {
-            float* q0 = r0 + n0;
-            float* q1 = r1 ? r1 + n0 : r0 + n0;
+            float* q0 = r0 + (n0 - off);
+            float* q1 = r1 ? r1 + (n0 - off) : q0;
             const bool two = r1 != nullptr;
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                if (!CROP || n0 + r * step < N) {
+                if (!CROP || (unsigned)(n0 + r * step - off) < len) {
                     st_stream(q0 + r * step, v[r].x);
                     pw0 = fmaf(v[r].x, v[r].x, pw0);
                     if (two) {
@@ -468,10 +471,10 @@ __device__ __forceinline__ WOut<CROP> make_wout(const Params& p, const Job& J, i
     o.pw0 = o.pw1 = 0.f;
     if (wav_real(p.wavelet)) {
         o.rc = nullptr;
-        o.r0 = (float*)p.W + (int64_t)J.g[0].row * p.N;
-        o.r1 = J.g[1].row >= 0 ? (float*)p.W + (int64_t)J.g[1].row * p.N : nullptr;
+        o.r0 = (float*)p.W + (int64_t)J.g[0].row * p.out_len;
+        o.r1 = J.g[1].row >= 0 ? (float*)p.W + (int64_t)J.g[1].row * p.out_len : nullptr;
     } else {
-        o.rc = (float2*)p.W + (int64_t)J.g[0].row * p.N;
+        o.rc = (float2*)p.W + (int64_t)J.g[0].row * p.out_len;
         o.r0 = o.r1 = nullptr;
     }
     return o;

@@ -13,6 +13,7 @@
 
 struct cwt_plan {
     int64_t N = 0, M = 0;
+    int64_t out_off = 0, out_len = 0;     // kept output window (out_len = N unless a sub-plan)
     int logM = 0, h = 0;
     int32_t S = 0;
     int wavelet = 0, boundary = 0;
@@ -92,6 +93,15 @@ struct cwt_plan {
     void* d_edge_rows = nullptr;          // per row: E and the offset of its h table
     float2* d_edge_h = nullptr;           // h(j) = sqrt(w~ dx) psi(w~ j), j in [-E, E]
     double* d_edge_delta = nullptr;       // per block: change of the row's sum of |W|^2
+
+    // periodic boundary, N not a power of two: the rows come from zero-boundary
+    // sub-plans of the periodically extended signal (rows sub_r0[i] ..), each
+    // keeping the window [E_i, E_i + N) of its outputs
+    std::vector<cwt_plan*> subs;
+    std::vector<int32_t> sub_r0;
+    std::vector<int64_t> sub_E;
+    int64_t ext_E = 0;                    // extension on each side of the shared buffer
+    void* d_ext = nullptr;                // N + 2 ext_E samples, the input's dtype
 
     std::string err;
 };

@@ -273,3 +273,31 @@ def test_zero_boundary_short_scales(env, N, wavelet, smin, smax, S, order, dtype
         assert np.linalg.norm(W[s, edge] - ref[s, edge]) <= 10 * TOL * np.linalg.norm(ref[s]) + 1e-12, s
     P = orc.wavelet_power(ref)
     assert np.max(np.abs(spec - P) / P) < 1e-4
+
+
+@pytest.mark.parametrize("N,wavelet,smin,smax,S,order,dtype", [
+    (1000, "gdw", 2.0, 250.0, 9, "asc", "f32"),
+    (1023, "morlet", 4.0, 300.0, 8, "asc", "f32"),
+    (997, "morlet", 4.0, 900.0, 7, "shuffled", "f32"),        # prime N, scales beyond N/4
+    (4097, "gdw", 2.0, 1000.0, 10, "desc", "f64"),
+    (100000, "morlet", 4.0, 25000.0, 12, "asc", "f32"),
+])
+def test_periodic_any_length(env, N, wavelet, smin, smax, S, order, dtype):
+    """Periodic boundary with N not a power of two: W and the power spectrum
+    against the oracle's N-point FFTCWT (its own Bluestein FFT)."""
+    _, _, orc = env
+    f = synth.lognormal_field(N, seed=N + 3)
+    sc = synth.log_scales(smin, smax, S)
+    if order == "desc":
+        sc = sc[::-1].copy()
+    elif order == "shuffled":
+        sc = sc[np.random.default_rng(2).permutation(S)]
+    W, spec, M = run_gpu(env, f, sc, wavelet, "periodic", dtype=dtype)
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=N)
+    assert rel_l2(W, ref) <= TOL
+    for s in range(S):
+        assert np.linalg.norm(W[s] - ref[s]) / np.linalg.norm(ref[s]) <= 10 * TOL, s
+    P = orc.wavelet_power(ref)
+    assert np.max(np.abs(spec - P) / P) < 1e-4
+    if wavelet == "gdw":
+        assert np.max(np.abs(W.imag)) == 0.0
