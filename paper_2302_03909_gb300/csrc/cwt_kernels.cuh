@@ -433,7 +433,7 @@ struct WOut {
     __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int cstride) {
         const int n0 = d0 + t + p->A * j;
         const int step = p->A * cstride;
-        const int off = (int)p->out_off;
+        const int off = CROP ? (int)p->out_off : 0;    // without the crop (M = N) the window is [0, N)
         const unsigned len = (unsigned)p->out_len;
         if (rc) {
             float2* q = rc + (n0 - off);
