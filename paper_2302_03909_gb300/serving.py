@@ -276,3 +276,31 @@ def poisson_trace(rate: float, seconds: float, seed: int = 20230213, log2n=(10, 
                            "periodic" if rng.random() < 0.5 else "zero", t))
         rid += 1
     return out
+
+
+def capture_batch(items, n_streams: int = 4):
+    """One CUDA graph over a batch of transforms.  ``items`` are (plan,
+    signal, W, spectrum) with device tensors allocated beforehand; the
+    transforms are dealt round-robin over ``n_streams`` streams (each plan
+    still forks its own side streams) and joined at the end.  Returns the
+    graph; ``graph.replay()`` runs the whole batch with one launch from the
+    host.  The plans see a capturing stream and record their kernels directly."""
+    import torch
+
+    import paper_2302_03909_gb300 as cwt
+    s0 = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s0):
+        start = torch.cuda.Event()
+        start.record(s0)
+        for st in streams:
+            st.wait_event(start)
+        for i, (plan, sig, W, sp) in enumerate(items):
+            st = streams[i % n_streams]
+            cwt.cwt_exec_with_power(plan, sig, W, sp, st)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            s0.wait_event(e)
+    return g
