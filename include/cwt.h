@@ -67,7 +67,10 @@ typedef enum {
 } cwt_wavelet;
 
 typedef enum {
-    CWT_BOUNDARY_PERIODIC = 0, /* M = N; N must be a power of two in this build */
+    CWT_BOUNDARY_PERIODIC = 0, /* the N-periodic FFTCWT.  N a power of two: M = N.  Otherwise (GDW and
+                                  Morlet only) the same result through zero-padded transforms of the
+                                  periodically extended signal; scales whose spectrum is not negligible
+                                  (1e-7) at the Nyquist frequency give CWT_ERR_UNSUPPORTED */
     CWT_BOUNDARY_ZERO = 1      /* zero padding to M = next power of two >= 2N (Eq. 40 context) */
 } cwt_boundary;
 
@@ -105,7 +108,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales,
 /* Frees the plan and its device memory (synchronises the device first).  NULL is OK. */
 cwt_status cwt_plan_destroy(cwt_plan* plan);
 
-/* M, the plan's device workspace in bytes, and whether W is complex
+/* M (the largest transform length for a periodic plan whose N is not a power
+ * of two), the plan's device workspace in bytes, and whether W is complex
  * (1: interleaved complex64, Morlet; 0: float32, the real wavelets).  Any out-pointer may be NULL. */
 cwt_status cwt_plan_info(const cwt_plan* plan, int64_t* fft_len, size_t* workspace_bytes,
                          int32_t* out_is_complex);
