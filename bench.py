@@ -60,6 +60,7 @@ def parse_args():
     # batching: many signals of uneven lengths, each with its own plan
     ap.add_argument("--batch", action="store_true", help="measure a batch of uneven-length signals")
     ap.add_argument("--batch-signals", type=int, default=512, help="batch: number of signals")
+    ap.add_argument("--batch-streams", type=int, default=16, help="batch: streams the graph spreads the signals over")
     return ap.parse_args()
 
 
@@ -302,7 +303,7 @@ def run_batch(args):
     (GDW) or 4 (Morlet) to N/4, the wavelet and the boundary 50/50, multi-tone
     plus noise with periods scaled to N.  Each signal has its own plan, created
     first and timed apart.  With the inputs resident in HBM, the whole batch is
-    captured once as a CUDA graph over --slots streams and replayed; the
+    captured once as a CUDA graph over --batch-streams streams and replayed; the
     baseline is one launch sequence per signal on one stream.  Prints one
     JSON line."""
     import torch
@@ -352,7 +353,7 @@ def run_batch(args):
 
     # one graph launch over the whole batch (captured once, replayed)
     t0 = time.perf_counter()
-    graph = serving.capture_batch(items, n_streams=args.slots)
+    graph = serving.capture_batch(items, n_streams=args.batch_streams)
     torch.cuda.synchronize()
     out["capture_s"] = time.perf_counter() - t0
     t_graph = timed(graph.replay)
@@ -372,7 +373,7 @@ def run_batch(args):
             "detail": out,
             "config": {"signals": len(reqs), "N": "log-uniform integers in [1024, 65536]", "n_scales": "16..96",
                        "scale_samples": units, "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],
-                       "streams": args.slots, "inputs": "resident in HBM",
+                       "streams": args.batch_streams, "inputs": "resident in HBM",
                        "plans": "one per signal, created before the timed runs",
                        "timed": "one CUDA-graph launch over the batch vs one launch sequence per signal"},
             "data": "synthetic"}
