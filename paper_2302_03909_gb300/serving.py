@@ -174,7 +174,9 @@ class Server:
         return p
 
     def _need(self, req: Request) -> int:
-        # a new instance's workspace counts against the budget while it is busy
+        # a new instance's workspace counts against the budget while it is busy;
+        # the size is known once the shape's first plan exists, so the first
+        # request of a never-seen shape is admitted on its own buffers only
         extra = 0 if self.cache.has_idle(req.key) else self._ws_guess.get(req.key, 0)
         return req.io_bytes + extra
 
