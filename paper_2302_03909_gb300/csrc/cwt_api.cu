@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <set>
 #include <cstdio>
 #include <cstring>
@@ -86,7 +88,7 @@ double wavelet_spectrum_const(int wavelet, double omega0) {
 }
 
 // [u_lo, u_hi] outside which |psi_hat| < eps * max |psi_hat|
-void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* u_hi) {
+void wavelet_band_scan(int wavelet, double omega0, double eps, double* u_lo, double* u_hi) {
     // the CBSW spectrum only decays as u^-4: scan further, more coarsely
     const bool slow = wavelet == CWT_WAVELET_CBSW;
     const double step = slow ? 1.0 / 64.0 : 1.0 / 1024.0, U = slow ? 8192.0 : 80.0;
@@ -102,6 +104,25 @@ void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* 
     if (lo > hi) { lo = hi = 0.0; }
     *u_lo = lo - 2 * step;
     *u_hi = hi + 2 * step;
+}
+
+// the scan depends only on (wavelet, omega0, eps): plans of one shape family reuse it
+void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* u_hi) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, double, double>, std::pair<double, double>> memo;
+    const auto key = std::make_tuple(wavelet, omega0, eps);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) {
+            *u_lo = it->second.first;
+            *u_hi = it->second.second;
+            return;
+        }
+    }
+    wavelet_band_scan(wavelet, omega0, eps, u_lo, u_hi);
+    std::lock_guard<std::mutex> lock(mu);
+    memo[key] = {*u_lo, *u_hi};
 }
 
 }  // namespace
