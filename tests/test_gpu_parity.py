@@ -301,3 +301,37 @@ def test_periodic_any_length(env, N, wavelet, smin, smax, S, order, dtype):
     assert np.max(np.abs(spec - P) / P) < 1e-4
     if wavelet == "gdw":
         assert np.max(np.abs(W.imag)) == 0.0
+
+
+@pytest.mark.parametrize("N,boundary,wavelet,smin,smax,S", [
+    (1 << 24, "zero", "morlet", 4.0, float(1 << 22), 8),      # M = 2^25, the largest plan: 4096-point pass 2, cropped
+    (1 << 25, "periodic", "gdw", 2.0, float(1 << 23), 8),     # M = 2^25 without the crop
+    (1 << 23, "zero", "gdw", 2.0, float(1 << 21), 6),         # M = 2^24: 2048-point pass 2
+])
+def test_maximum_sizes_sampled(env, N, boundary, wavelet, smin, smax, S):
+    """The largest transforms a plan accepts (M up to 2^25): sampled outputs
+    against the oracle one by one, and the power spectrum against the mean of
+    |W|^2 over the whole device array."""
+    torch, cwt, orc = env
+    f = synth.lognormal_field(N, seed=N + 11)
+    sc = synth.log_scales(smin, smax, S)
+    plan = cwt.cwt_plan_create(N, sc, wavelet, boundary)
+    M = plan.M
+    assert M == (2 * N if boundary == "zero" else N)
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    W, spec = cwt.cwt_exec_with_power(plan, sig)
+    ps, pn = synth.sample_points(S, N, 32, seed=N + S)
+    got = W[torch.from_numpy(ps).long().cuda(), torch.from_numpy(pn).cuda()]
+    P_dev = (W.abs().double() ** 2).mean(dim=1)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy().astype(np.complex128)
+    assert np.all(np.isfinite(got))
+    ref = orc.cwt_fft_points(f32(f), sc, wavelet, ps, pn, M=M)
+    assert rel_l2(got, ref) <= TOL
+    if wavelet == "gdw":
+        assert np.max(np.abs(got.imag)) == 0.0
+    P = P_dev.cpu().numpy()
+    assert np.all(P > 0)
+    assert np.max(np.abs(spec.cpu().numpy() - P) / P) < 1e-5
+    del W, spec, P_dev
+    plan.close()
