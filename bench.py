@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--workload", default="lognormal_n1m_morlet_s64", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fft-baseline", action="store_true",
+                    help="skip the comparison with the library FFT (torch.fft / cuFFT) written the usual way")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     # narrower cases of a workload for profiler captures (not a bench line)
@@ -227,6 +229,92 @@ def cpu_baseline(name, budget_s, steps=1, warmup=0):
             "sample": f"{n_sub} of {len(sc)} scales (evenly spread) x {len(w['boundaries'])} boundaries, "
                       f"N={N}, FP64 FFT tier, OpenMP over scales; {t:.1f} s per sample",
             "seconds": t}
+
+
+def fft_library_baseline(f, sc, wavelet, plans, outs, flush, stream, steps, warmup=2):
+    """The same transforms written the usual way on the GPU with the library FFT
+    (torch.fft, i.e. cuFFT).  Set-up, untimed: the wavelet spectra
+    sqrt(s) psi_hat(2 pi m~ s / M) of Eq. 10 for every scale, kept in HBM.
+    Step: one forward FFT per boundary; per chunk of scales the product with the
+    spectrum and a batched inverse FFT (C2R for the real GDW, C2C for the
+    Morlet), written straight into W when M = N and cropped to the first N
+    outputs otherwise; the power spectrum as row norms of W.  Timed like the
+    library's steps (CUDA events on the stream, the L2 flushed between steps).
+    A comparison baseline only: the library itself never calls it."""
+    import torch
+    dev = outs[0][0].device
+    N, S = len(f), len(sc)
+    real = wavelet == "gdw"
+    if wavelet not in ("gdw", "morlet"):
+        raise ValueError(wavelet)
+    omega0 = 6.0
+    if real:   # Table 2: GDW, C_N = (18 pi)^(-1/4)
+        cn = (18.0 * math.pi) ** -0.25
+    else:      # Morlet with the correction term, unit energy
+        cn = math.pi ** -0.25 / math.sqrt(1.0 - 2.0 * math.exp(-0.75 * omega0 ** 2) + math.exp(-omega0 ** 2))
+
+    def psi_hat(k):
+        if real:
+            return (8.0 * math.sqrt(math.pi) * cn) * k * k * torch.exp(-k * k)
+        return (math.sqrt(2.0 * math.pi) * cn) * (torch.exp(-0.5 * (k - omega0) ** 2)
+                                                   - torch.exp(-0.5 * (k * k + omega0 ** 2)))
+
+    sig = torch.tensor(f, dtype=torch.float32, device=dev)
+    sd = torch.tensor(np.asarray(sc, dtype=np.float64), dtype=torch.float64, device=dev)
+    res = []
+    for p in plans:
+        M = p.M
+        nb = M // 2 + 1 if real else M
+        mi = torch.arange(nb, device=dev, dtype=torch.float64)
+        mt = mi if real else torch.where(2 * mi <= M, mi, mi - M)     # signed frequency
+        chunk = max(1, min(S, (256 << 20) // (nb * 8)))
+        Psi = torch.empty(S, nb, dtype=torch.float32, device=dev)
+        for c0 in range(0, S, chunk):
+            s_ = sd[c0:c0 + chunk, None]
+            Psi[c0:c0 + chunk] = (torch.sqrt(s_) * psi_hat(mt[None, :] * (2.0 * math.pi / M) * s_)).float()
+        res.append((M, chunk, Psi, p.empty_output(dev), torch.empty(S, dtype=torch.float64, device=dev)))
+
+    def step():
+        for M, chunk, Psi, W, sp in res:
+            # rfft: the conjugate of the paper's e^{+} spectrum on [0, M/2]; ifft: that spectrum / M
+            F = torch.fft.rfft(sig, n=M) if real else torch.fft.ifft(sig, n=M)
+            for c0 in range(0, S, chunk):
+                X = F[None, :] * Psi[c0:c0 + chunk]
+                inv = (lambda x, **kw: torch.fft.irfft(x, n=M, **kw)) if real else torch.fft.fft
+                if M == N:
+                    inv(X, out=W[c0:c0 + chunk])
+                else:
+                    W[c0:c0 + chunk] = inv(X)[:, :N]
+            torch.square(torch.linalg.vector_norm(W, dim=1).double(), out=sp)
+            sp.div_(N)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    # the same outputs as the library's (its last step): like is timed against like
+    err = 0.0
+    err_p = 0.0
+    for (M, chunk, Psi, W, sp), (Wo, spo) in zip(res, outs):
+        d = torch.linalg.vector_norm((W - Wo).reshape(-1)) / torch.linalg.vector_norm(Wo.reshape(-1))
+        err = max(err, float(d))
+        err_p = max(err_p, float(((sp - spo).abs() / spo).max()))
+    units = S * N * len(plans)
+    out = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "rel_l2_vs_library": err, "power_max_rel_dev_vs_library": err_p,
+           "what": "torch.fft (cuFFT), FP32: wavelet spectra precomputed in HBM (untimed); per step a "
+                   "forward FFT per boundary, per chunk of scales one product and a batched C2R (GDW) or "
+                   "C2C (Morlet) inverse into W (cropped copy for the zero boundary), power as row norms"}
+    del res
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -488,6 +576,10 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": te * 1e3 / e2e_steps}
 
+    fftb = None
+    if rank == 0 and world == 1 and not args.no_fft_baseline:
+        fftb = fft_library_baseline(f, sc, w["wavelet"], plans, outs, flush, stream, min(args.steps, 10))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.workload, args.cpu_seconds)
@@ -521,6 +613,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "fft_library_baseline": fftb,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)
