@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct cwt_plan cwt_plan; /* opaque; created and destroyed by the library */
+typedef struct cwt_batch cwt_batch; /* opaque; see cwt_batch_create */
 
 typedef enum {
     CWT_OK = 0,
@@ -230,6 +231,43 @@ cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t kernel_class, double* tot
 #define CWT_NOALLOC_CHUNK 32768
 cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, int32_t n_scales, int32_t is_complex,
                                      double* spectrum_dev, void* stream);
+
+/* Batches of many transforms (signals of uneven lengths, each with its own
+ * plan) run as a few grouped launches instead of one launch sequence per plan.
+ *
+ * cwt_batch_create binds plans[i] to its own device buffers signals_dev[i],
+ * W_dev[i] and spectra_dev[i] (as cwt_exec_with_power takes them; spectra_dev
+ * may be NULL, or hold NULL entries, for no power spectrum).  It records every
+ * plan's launch sequence with the dependency level of each launch (its depth
+ * in the plan's stream and event order) and merges, over all plans, the
+ * launches of one kernel at one level into one grid: a per-CTA table gives
+ * each CTA its plan's kernel argument and its block coordinates in the launch
+ * it came from.  The CTAs compute exactly what the plan's own launches would,
+ * so cwt_batch_exec writes, bit for bit, the results of calling
+ * cwt_exec_with_power on each plan.  The result is the FFTCWT of Eqs. 8-10
+ * and the power of Eq. 42 for every signal; the grouping is this library's
+ * scheduling and has no counterpart in the paper.
+ *
+ * Every plan may appear once (its workspace is its own); timing must be off;
+ * all plans belong to the current device.  n_streams (1..8) is the number of
+ * streams a level's grouped launches are spread over.  The batch holds device
+ * tables of about 4 bytes per CTA plus the launch arguments; the plans and
+ * buffers stay owned by the caller and must outlive the batch, and a plan must
+ * not run elsewhere while its batch runs.
+ *
+ * cwt_batch_exec runs the levels in order on `stream` (asynchronous; the
+ * groups of a level fork to the batch's own streams and join back).
+ * cwt_batch_info reports the number of levels, grouped launches and CTAs, and
+ * the number of plan launches they replace; any out-pointer may be NULL.
+ * Errors: CWT_ERR_INVALID_ARG for bad arguments (a NULL or repeated plan, a
+ * bad buffer, n < 1, n_streams outside 1..8, another device), CWT_ERR_OOM or
+ * CWT_ERR_CUDA if the tables cannot be made. */
+cwt_status cwt_batch_create(cwt_batch** batch, cwt_plan* const* plans, const void* const* signals_dev,
+                            void* const* W_dev, double* const* spectra_dev, int32_t n, int32_t n_streams);
+cwt_status cwt_batch_exec(cwt_batch* batch, void* stream);
+cwt_status cwt_batch_info(const cwt_batch* batch, int32_t* n_levels, int32_t* n_launches, int64_t* n_ctas,
+                          int64_t* n_plan_launches);
+cwt_status cwt_batch_destroy(cwt_batch* batch);
 
 /* Static description of a status code. */
 const char* cwt_status_string(cwt_status status);

@@ -24,6 +24,7 @@ __all__ = [
     "cwt_exec_with_power", "cwt_wavelet_power", "cwt_env_power", "cwt_icwt", "cwt_exec_host",
     "cwt_scales_paper_grid",
     "cwt_status_string", "cwt_wavelet_power_noalloc", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
+    "Batch", "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy",
     "ABI_FUNCTIONS", "KERNEL_CLASSES",
 ]
 
@@ -38,6 +39,7 @@ ABI_FUNCTIONS = [
     "cwt_plan_info", "cwt_exec", "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host",
     "cwt_scales_paper_grid", "cwt_status_string", "cwt_plan_last_error", "cwt_plan_set_timing",
     "cwt_plan_get_timing", "cwt_wavelet_power_noalloc", "cwt_env_power", "cwt_icwt",
+    "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy",
 ]
 NOALLOC_MAX_PARTIALS = 65536
 NOALLOC_CHUNK = 32768
@@ -106,6 +108,16 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.cwt_env_power.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.cwt_icwt.restype = ctypes.c_int
         lib.cwt_icwt.argtypes = [vp, vp, vp, vp]
+        pvp = ctypes.POINTER(vp)
+        lib.cwt_batch_create.restype = ctypes.c_int
+        lib.cwt_batch_create.argtypes = [ctypes.POINTER(vp), pvp, pvp, pvp, pvp, i32, i32]
+        lib.cwt_batch_exec.restype = ctypes.c_int
+        lib.cwt_batch_exec.argtypes = [vp, vp]
+        lib.cwt_batch_info.restype = ctypes.c_int
+        lib.cwt_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                       ctypes.POINTER(i64)]
+        lib.cwt_batch_destroy.restype = ctypes.c_int
+        lib.cwt_batch_destroy.argtypes = [vp]
         _lib = lib
         return lib
 
@@ -363,3 +375,74 @@ def cwt_scales_paper_grid(N: int, wavelet: str = "gdw", omega0: float = 6.0,
                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      ctypes.byref(n)))
     return out
+
+
+class Batch:
+    """A cwt_batch handle.  Keeps the plans and tensors it was bound to alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def exec(self, stream=None):
+        cwt_batch_exec(self, stream)
+
+    def info(self) -> dict:
+        return cwt_batch_info(self)
+
+    def close(self):
+        cwt_batch_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cwt_batch_create(items, n_streams: int = 4) -> Batch:
+    """One batch over items = [(plan, signal, W, spectrum or None), ...]: each
+    plan bound to its own device tensors, as cwt_exec_with_power takes them."""
+    n = len(items)
+    if n < 1:
+        raise ValueError("a batch needs at least one item")
+    plans = (ctypes.c_void_p * n)()
+    sigs = (ctypes.c_void_p * n)()
+    Ws = (ctypes.c_void_p * n)()
+    sps = (ctypes.c_void_p * n)()
+    for i, (plan, signal, W, spectrum) in enumerate(items):
+        _check_signal(plan, signal)
+        _check_W(plan, W)
+        plans[i] = plan._h
+        sigs[i] = _dev_ptr(signal, "signal").value
+        Ws[i] = _dev_ptr(W, "W").value
+        if spectrum is not None:
+            import torch
+            if spectrum.dtype != torch.float64 or spectrum.numel() != plan.n_scales:
+                raise ValueError(f"spectrum must hold {plan.n_scales} float64 values")
+            sps[i] = _dev_ptr(spectrum, "spectrum").value
+    h = ctypes.c_void_p()
+    st = load_library().cwt_batch_create(ctypes.byref(h), plans, sigs, Ws, sps, n, int(n_streams))
+    _check(st, items[0][0] if st not in (0,) else None)
+    return Batch(h, list(items))
+
+
+def cwt_batch_exec(batch: Batch, stream=None):
+    if not batch._h:
+        raise ValueError("batch is closed")
+    _check(load_library().cwt_batch_exec(batch._h, _stream_ptr(stream)))
+
+
+def cwt_batch_info(batch: Batch) -> dict:
+    lv, nl = ctypes.c_int32(), ctypes.c_int32()
+    ct, rec = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().cwt_batch_info(batch._h, ctypes.byref(lv), ctypes.byref(nl), ctypes.byref(ct),
+                                         ctypes.byref(rec)))
+    return {"levels": lv.value, "launches": nl.value, "ctas": ct.value, "plan_launches": rec.value}
+
+
+def cwt_batch_destroy(batch: Batch):
+    if batch._h:
+        load_library().cwt_batch_destroy(batch._h)
+        batch._h = None
+        batch._keep = None

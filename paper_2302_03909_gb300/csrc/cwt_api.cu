@@ -131,9 +131,17 @@ void wavelet_band(int wavelet, double omega0, double eps, double* u_lo, double* 
 // F(M - k) above: real signal), transposed to Ft[b A + a] so that the wide
 // scales' pass 1 reads each column b contiguously.  32 x 32 tiles through
 // shared memory; grid (ceil(L / 32), ceil(A / 32)), block (32, 8).
-static __global__ void k_spec_transpose(const float2* __restrict__ Fp, float2* __restrict__ Ft, int M, int L, int A) {
+struct TransposeArgs {
+    const float2* Fp;
+    float2* Ft;
+    int32_t M, L, A, pad_;
+};
+__device__ __forceinline__ void spec_transpose_body(const TransposeArgs& ta, const Cta c) {
+    const float2* __restrict__ Fp = ta.Fp;
+    float2* __restrict__ Ft = ta.Ft;
+    const int M = ta.M, L = ta.L, A = ta.A;
     __shared__ float2 tile[32][33];
-    const int b0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+    const int b0 = c.x * 32, a0 = c.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
         const int a = a0 + i, b = b0 + tx;
@@ -154,6 +162,12 @@ static __global__ void k_spec_transpose(const float2* __restrict__ Fp, float2* _
         const int b = b0 + i, a = a0 + tx;
         if (a < A && b < L) Ft[(int64_t)b * A + a] = tile[tx][i];
     }
+}
+static __global__ void k_spec_transpose(TransposeArgs a) { spec_transpose_body(a, cta_plain()); }
+static __global__ void k_spec_transpose_g(GroupMap g) {
+    Cta c;
+    const TransposeArgs& a = group_args<TransposeArgs>(g, c);
+    spec_transpose_body(a, c);
 }
 
 // ------------------------------------------------ zero boundary, short wavelets
@@ -186,19 +200,33 @@ __device__ __forceinline__ float load_f(const void* signal, int f64, int64_t m) 
     return f64 ? (float)__ldg(&((const double*)signal)[m]) : __ldg(&((const float*)signal)[m]);
 }
 
+struct EdgeFixArgs {
+    const void* signal;
+    void* W;
+    const float2* h;
+    const EdgeRow* rows;
+    double* delta;
+    int64_t N;
+    int32_t sig_f64, do_power;
+};
 template <bool CPLX>
-static __global__ void __launch_bounds__(kEdgeThreads)
-    k_edge_fix(const void* __restrict__ signal, int sig_f64, int64_t N, void* W, const float2* __restrict__ h,
-               const EdgeRow* __restrict__ rows, double* __restrict__ delta, int do_power) {
+__device__ __forceinline__ void edge_fix_body(const EdgeFixArgs& ea, const Cta c) {
+    const void* __restrict__ signal = ea.signal;
+    const int sig_f64 = ea.sig_f64;
+    const int64_t N = ea.N;
+    void* W = ea.W;
+    const float2* __restrict__ h = ea.h;
+    const EdgeRow* __restrict__ rows = ea.rows;
+    double* __restrict__ delta = ea.delta;
     __shared__ float fs[kEdgeKT + kEdgeOut];
     __shared__ float2 hs[kEdgeKT + kEdgeOut];
     __shared__ float2 part[kEdgeSplit][kEdgeOut];
     __shared__ double red[2 * (kEdgeThreads / 32)];
-    const int r = blockIdx.y;
+    const int r = c.y;
     const EdgeRow er = rows[r];
     const int E = er.E;
-    const bool left = (blockIdx.x & 1) == 0;
-    const int i0 = (blockIdx.x >> 1) * kEdgeOut;
+    const bool left = (c.x & 1) == 0;
+    const int i0 = (c.x >> 1) * kEdgeOut;
     const int o = threadIdx.x % kEdgeOut, q = threadIdx.x / kEdgeOut;
     const int i = i0 + o;
     const float2* hr = h + er.h_off + E;              // hr[j], j in [-E, E]
@@ -273,19 +301,41 @@ static __global__ void __launch_bounds__(kEdgeThreads)
             }
         }
     }
-    if (do_power) {
+    if (ea.do_power) {
         double s0, s1;
         block_sum2<kEdgeThreads>(dpow, 0.f, &s0, &s1, red);
-        if (threadIdx.x == 0) delta[(int64_t)r * gridDim.x + blockIdx.x] = s0;
+        if (threadIdx.x == 0) delta[(int64_t)r * c.nx + c.x] = s0;
     }
+}
+template <bool CPLX>
+static __global__ void __launch_bounds__(kEdgeThreads) k_edge_fix(EdgeFixArgs a) {
+    edge_fix_body<CPLX>(a, cta_plain());
+}
+template <bool CPLX>
+static __global__ void __launch_bounds__(kEdgeThreads) k_edge_fix_g(GroupMap g) {
+    Cta c;
+    const EdgeFixArgs& a = group_args<EdgeFixArgs>(g, c);
+    edge_fix_body<CPLX>(a, c);
 }
 
 // spectrum[r] += (sum of the row's block changes, fixed order) / N
-static __global__ void k_edge_power(const double* __restrict__ delta, int bpr, int64_t N, double* __restrict__ spectrum) {
+struct EdgePowerArgs {
+    const double* delta;
+    double* spectrum;
+    int64_t N;
+    int32_t bpr, pad_;
+};
+__device__ __forceinline__ void edge_power_body(const EdgePowerArgs& a, const Cta c) {
     if (threadIdx.x != 0) return;
     double acc = 0.0;
-    for (int b = 0; b < bpr; b++) acc += delta[(int64_t)blockIdx.x * bpr + b];
-    spectrum[blockIdx.x] += acc / (double)N;
+    for (int b = 0; b < a.bpr; b++) acc += a.delta[(int64_t)c.x * a.bpr + b];
+    a.spectrum[c.x] += acc / (double)a.N;
+}
+static __global__ void k_edge_power(EdgePowerArgs a) { edge_power_body(a, cta_plain()); }
+static __global__ void k_edge_power_g(GroupMap g) {
+    Cta c;
+    const EdgePowerArgs& a = group_args<EdgePowerArgs>(g, c);
+    edge_power_body(a, c);
 }
 
 namespace {
@@ -312,14 +362,25 @@ void psi_x(int wavelet, double omega0, double x, double* re, double* im) {
 
 // Periodic boundary with N not a power of two: ext[m] = f((m - E) mod N),
 // m < N + 2E, the signal extended periodically by E samples on each side.
-static __global__ void k_periodic_extend(const void* __restrict__ f, int f64, int64_t N, int64_t E,
-                                         void* __restrict__ ext) {
-    const int64_t total = N + 2 * E;
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < total; m += (int64_t)gridDim.x * blockDim.x) {
+struct ExtendArgs {
+    const void* f;
+    void* ext;
+    int64_t N, E;
+    int32_t f64, pad_;
+};
+__device__ __forceinline__ void periodic_extend_body(const ExtendArgs& a, const Cta c) {
+    const int64_t N = a.N, E = a.E, total = N + 2 * E;
+    for (int64_t m = c.x * (int64_t)blockDim.x + threadIdx.x; m < total; m += (int64_t)c.nx * blockDim.x) {
         const int64_t src = ((m - E) % N + N) % N;
-        if (f64) ((double*)ext)[m] = __ldg(&((const double*)f)[src]);
-        else ((float*)ext)[m] = __ldg(&((const float*)f)[src]);
+        if (a.f64) ((double*)a.ext)[m] = __ldg(&((const double*)a.f)[src]);
+        else ((float*)a.ext)[m] = __ldg(&((const float*)a.f)[src]);
     }
+}
+static __global__ void k_periodic_extend(ExtendArgs a) { periodic_extend_body(a, cta_plain()); }
+static __global__ void k_periodic_extend_g(GroupMap g) {
+    Cta c;
+    const ExtendArgs& a = group_args<ExtendArgs>(g, c);
+    periodic_extend_body(a, c);
 }
 
 // ====================================================================== plan
@@ -739,9 +800,29 @@ cwt_status opt_in_smem(cwt_plan* p, const void* fn) {
     return CWT_OK;
 }
 
+// Stream-order operations of a launch sequence: made, or recorded by a batch.
+cwt_status ev_record(cwt_plan* p, cudaEvent_t e, cudaStream_t s) {
+    if (p->rec) p->rec->record(e, s);
+    else CWT_CUDA(p, cudaEventRecord(e, s));
+    return CWT_OK;
+}
+cwt_status ev_wait(cwt_plan* p, cudaStream_t s, cudaEvent_t e) {
+    if (p->rec) p->rec->wait(s, e);
+    else CWT_CUDA(p, cudaStreamWaitEvent(s, e, 0));
+    return CWT_OK;
+}
+template <class A>
+void rec_launch(cwt_plan* p, const void* gfn, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const A& a) {
+    p->rec->add(s, gfn, grid, block, smem, &a, sizeof(A));
+}
+
 cwt_status launch(cwt_plan* p, const Entry& e, dim3 grid, size_t smem, const Params& P, cudaStream_t s, int cls,
                   double bytes) {
-    if (!e.fn) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
+    if (!e.fn || !e.gfn) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
+    if (p->rec) {
+        rec_launch(p, (const void*)e.gfn, grid, dim3(e.NT), smem, s, P);
+        return CWT_OK;
+    }
     cwt_status st = opt_in_smem(p, (const void*)e.fn);
     if (st != CWT_OK) return st;
     LaunchTimer lt(p, cls, bytes, s);
@@ -769,9 +850,14 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
             const int64_t total = p->N + 2 * p->ext_E;
             const unsigned blocks = (unsigned)std::min<int64_t>(4096, (total + 255) / 256);
-            k_periodic_extend<<<blocks, 256, 0, s>>>(signal, f64, p->N, p->ext_E, p->d_ext);
-            CWT_CUDA(p, cudaGetLastError());
-            lt.done();
+            const ExtendArgs a{signal, p->d_ext, p->N, p->ext_E, f64, 0};
+            if (p->rec) {
+                rec_launch(p, (const void*)k_periodic_extend_g, dim3(blocks), dim3(256), 0, s, a);
+            } else {
+                k_periodic_extend<<<blocks, 256, 0, s>>>(a);
+                CWT_CUDA(p, cudaGetLastError());
+                lt.done();
+            }
         }
         for (size_t i = 0; i < p->subs.size(); i++) {
             const void* sig = (const char*)p->d_ext + (size_t)(p->ext_E - p->sub_E[i]) * se;
@@ -799,20 +885,28 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             const dim3 grid((unsigned)p->edge_bpr, (unsigned)p->child_n);
             const EdgeRow* rows = (const EdgeRow*)p->d_edge_rows;
             const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
-            if (p->wavelet == CWT_WAVELET_MORLET)
-                k_edge_fix<true><<<grid, kEdgeThreads, 0, es>>>(signal, f64, p->N, Wc, p->d_edge_h, rows, p->d_edge_delta,
-                                                                sc != nullptr);
-            else
-                k_edge_fix<false><<<grid, kEdgeThreads, 0, es>>>(signal, f64, p->N, Wc, p->d_edge_h, rows,
-                                                                 p->d_edge_delta, sc != nullptr);
-            CWT_CUDA(p, cudaGetLastError());
-            lt.done();
+            const EdgeFixArgs a{signal, Wc, p->d_edge_h, rows, p->d_edge_delta, p->N, f64, sc != nullptr};
+            const bool cplx = p->wavelet == CWT_WAVELET_MORLET;
+            if (p->rec) {
+                rec_launch(p, cplx ? (const void*)k_edge_fix_g<true> : (const void*)k_edge_fix_g<false>, grid,
+                           dim3(kEdgeThreads), 0, es, a);
+            } else {
+                if (cplx) k_edge_fix<true><<<grid, kEdgeThreads, 0, es>>>(a);
+                else k_edge_fix<false><<<grid, kEdgeThreads, 0, es>>>(a);
+                CWT_CUDA(p, cudaGetLastError());
+                lt.done();
+            }
         }
         if (sc) {
             LaunchTimer lt(p, CWT_KCLASS_POWER, 0.0, es);
-            k_edge_power<<<p->child_n, 32, 0, es>>>(p->d_edge_delta, p->edge_bpr, p->N, sc);
-            CWT_CUDA(p, cudaGetLastError());
-            lt.done();
+            const EdgePowerArgs a{p->d_edge_delta, sc, p->N, p->edge_bpr, 0};
+            if (p->rec) {
+                rec_launch(p, (const void*)k_edge_power_g, dim3(p->child_n), dim3(32), 0, es, a);
+            } else {
+                k_edge_power<<<p->child_n, 32, 0, es>>>(a);
+                CWT_CUDA(p, cudaGetLastError());
+                lt.done();
+            }
         }
         return CWT_OK;
     };
@@ -822,8 +916,8 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     }
     cudaStream_t fs = s;                         // stream of this plan's forward transform
     if (p->child) {
-        CWT_CUDA(p, cudaEventRecord(p->ev_pre, s));
-        CWT_CUDA(p, cudaStreamWaitEvent(p->side[0], p->ev_pre, 0));
+        if ((st = ev_record(p, p->ev_pre, s)) != CWT_OK) return st;
+        if ((st = ev_wait(p, p->side[0], p->ev_pre)) != CWT_OK) return st;
         fs = p->side[0];
     }
 
@@ -852,9 +946,13 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     // the band jobs' values Z(k), once per call (each band CTA reads its job's table)
     if (p->n_band_jobs > 0) {
         LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, fs);
-        k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, fs>>>(P);
-        CWT_CUDA(p, cudaGetLastError());
-        lt.done();
+        if (p->rec) {
+            rec_launch(p, (const void*)k_band_table_g, dim3((unsigned)p->n_band_jobs), dim3(256), 0, fs, P);
+        } else {
+            k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, fs>>>(P);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
     }
 
     // the wide scales' pass 1 reads the spectrum column by column: transpose it once
@@ -862,15 +960,21 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         const int L = 1 << p->wide_logl;
         const int A = (int)(p->M >> p->wide_logl);
         LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, fs);
-        k_spec_transpose<<<dim3((L + 31) / 32, (A + 31) / 32), dim3(32, 8), 0, fs>>>(p->d_Fp, p->d_Ft, (int)p->M, L, A);
-        CWT_CUDA(p, cudaGetLastError());
-        lt.done();
+        const TransposeArgs a{p->d_Fp, p->d_Ft, (int32_t)p->M, L, A, 0};
+        const dim3 grid((L + 31) / 32, (A + 31) / 32);
+        if (p->rec) {
+            rec_launch(p, (const void*)k_spec_transpose_g, grid, dim3(32, 8), 0, fs, a);
+        } else {
+            k_spec_transpose<<<grid, dim3(32, 8), 0, fs>>>(a);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
     }
 
     if (p->child) {
-        CWT_CUDA(p, cudaEventRecord(p->ev_pfwd, fs));
+        if ((st = ev_record(p, p->ev_pfwd, fs)) != CWT_OK) return st;
         if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
-        CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_pfwd, 0));
+        if ((st = ev_wait(p, s, p->ev_pfwd)) != CWT_OK) return st;
     }
 
     // 2-3. band scales (one launch per DFT length) and wide-scale batches
@@ -882,10 +986,10 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     const int nstreams = std::min(nwork, cwt_plan::kSide + 1);
     cudaStream_t streams[cwt_plan::kSide + 1] = {s};
     if (nstreams > 1) {
-        CWT_CUDA(p, cudaEventRecord(p->ev_fork, s));
+        if ((st = ev_record(p, p->ev_fork, s)) != CWT_OK) return st;
         for (int i = 1; i < nstreams; i++) {
             streams[i] = p->side[i - 1];
-            CWT_CUDA(p, cudaStreamWaitEvent(streams[i], p->ev_fork, 0));
+            if ((st = ev_wait(p, streams[i], p->ev_fork)) != CWT_OK) return st;
         }
     }
     if (p->child && (st = edge_fix(streams[nstreams - 1])) != CWT_OK) return st;
@@ -911,12 +1015,18 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             const int A1 = Q.A >> wb.logl1;
             const int tpb = (A1 + e1.T - 1) / e1.T;
             size_t smem = (size_t)(1 << wb.logl1) * sizeof(float2) + stage_smem(wb.logl1, e1.T);
-            if (!e1.fn) return fail(p, CWT_ERR_INTERNAL, "missing pass-1 instantiation");
-            if ((st = opt_in_smem(p, (const void*)e1.fn)) != CWT_OK) return st;
-            LaunchTimer lt(p, CWT_KCLASS_WIDE1, wb.band_bytes, ws);
-            e1.fn<<<dim3(L * tpb, wb.count), e1.NT, smem, ws>>>(Q, L, tpb);
-            CWT_CUDA(p, cudaGetLastError());
-            lt.done();
+            if (!e1.fn || !e1.gfn) return fail(p, CWT_ERR_INTERNAL, "missing pass-1 instantiation");
+            const Wide1pArgs a{Q, L, tpb, {0, 0}};
+            const dim3 grid(L * tpb, wb.count);
+            if (p->rec) {
+                rec_launch(p, (const void*)e1.gfn, grid, dim3(e1.NT), smem, ws, a);
+            } else {
+                if ((st = opt_in_smem(p, (const void*)e1.fn)) != CWT_OK) return st;
+                LaunchTimer lt(p, CWT_KCLASS_WIDE1, wb.band_bytes, ws);
+                e1.fn<<<grid, e1.NT, smem, ws>>>(a);
+                CWT_CUDA(p, cudaGetLastError());
+                lt.done();
+            }
         }
         Q.D = p->wide_D;
         const int tiles2 = (Q.A + e2.T - 1) / e2.T;
@@ -936,16 +1046,22 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
     }
     for (int i = 1; i < nstreams; i++) {
-        CWT_CUDA(p, cudaEventRecord(p->ev_join[i - 1], streams[i]));
-        CWT_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[i - 1], 0));
+        if ((st = ev_record(p, p->ev_join[i - 1], streams[i])) != CWT_OK) return st;
+        if ((st = ev_wait(p, s, p->ev_join[i - 1])) != CWT_OK) return st;
     }
 
     // 4. power spectrum: fixed-order reduction of the per-tile partials
     if (spectrum) {
         LaunchTimer lt(p, CWT_KCLASS_POWER, 8.0 * (double)(p->n_partials + p->S), s);
-        k_power_finalize<<<p->S, 32, 0, s>>>(p->d_partials, p->d_part_off, p->d_part_cnt, p->S, p->out_len, spectrum);
-        CWT_CUDA(p, cudaGetLastError());
-        lt.done();
+        if (p->rec) {
+            const PowerArgs a{p->d_partials, p->d_part_off, p->d_part_cnt, spectrum, p->out_len, p->S, 0};
+            rec_launch(p, (const void*)k_power_finalize_g, dim3(p->S), dim3(32), 0, s, a);
+        } else {
+            k_power_finalize<<<p->S, 32, 0, s>>>(p->d_partials, p->d_part_off, p->d_part_cnt, p->S, p->out_len,
+                                                 spectrum);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
     }
     return CWT_OK;
 }
@@ -1075,6 +1191,61 @@ cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* sc
     *plan = p;
     return CWT_OK;
 }
+
+// ==================================================================== batches
+
+// A batch runs the launch sequences of several plans, each bound to its own
+// signal, W and spectrum, as grouped launches.  Every plan's launches are
+// recorded with their dependency levels (Recorder); the launches of one kernel
+// instantiation at one level, from all plans, become one grid whose CTAs find
+// their own launch's argument and block coordinates through a per-CTA index
+// (GroupMap).  The levels run one after another on the call's stream; the
+// groups of a level are spread over n_streams streams.
+constexpr int kBatchMaxStreams = 8;
+
+struct cwt_batch {
+    int device = -1;
+    struct Group {
+        const void* gfn;
+        dim3 block;
+        size_t smem;
+        int level;
+        int64_t ctas;
+        int32_t stride;
+        size_t args_off, geom_off, sub_off;     // byte offsets into d_buf
+    };
+    std::vector<Group> groups;                  // in level order
+    std::vector<int> level_first;               // groups of level l: [level_first[l], level_first[l + 1])
+    unsigned char* d_buf = nullptr;
+    int n_streams = 1;
+    cudaStream_t side[kBatchMaxStreams] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBatchMaxStreams] = {};
+    int64_t recorded = 0, ctas = 0;
+};
+
+namespace {
+
+void set_rec(cwt_plan* p, Recorder* r) {
+    p->rec = r;
+    if (p->child) set_rec(p->child, r);
+    for (cwt_plan* q : p->subs) set_rec(q, r);
+}
+
+void free_batch(cwt_batch* b) {
+    if (!b) return;
+    if (b->d_buf) cudaFree(b->d_buf);
+    for (int i = 0; i < kBatchMaxStreams; i++) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    delete b;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+}  // namespace
 
 // ====================================================================== ABI
 
@@ -1344,6 +1515,170 @@ cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t cls, double* total_ms, in
     if (total_ms) *total_ms = plan->t_ms[cls] + cm;
     if (launches) *launches = plan->t_launches[cls] + cn;
     if (algorithmic_bytes) *algorithmic_bytes = plan->t_bytes[cls] + cb;
+    return CWT_OK;
+}
+
+cwt_status cwt_batch_create(cwt_batch** batch, cwt_plan* const* plans, const void* const* signals_dev,
+                            void* const* W_dev, double* const* spectra_dev, int32_t n, int32_t n_streams) {
+    if (!batch) return CWT_ERR_INVALID_ARG;
+    *batch = nullptr;
+    if (!plans || !signals_dev || !W_dev || n < 1 || n_streams < 1 || n_streams > kBatchMaxStreams)
+        return CWT_ERR_INVALID_ARG;
+    std::set<const cwt_plan*> seen;
+    for (int32_t i = 0; i < n; i++) {
+        cwt_plan* p = plans[i];
+        if (!p || !seen.insert(p).second) return CWT_ERR_INVALID_ARG;      // each plan once: its workspace is its own
+        cwt_status st = check_exec_args(p, signals_dev[i], W_dev[i]);
+        if (st != CWT_OK) return st;
+        double* sp = spectra_dev ? spectra_dev[i] : nullptr;
+        if (sp && !aligned(sp, 8)) return fail(p, CWT_ERR_INVALID_ARG, "bad spectrum pointer");
+        if (p->timing) return fail(p, CWT_ERR_INVALID_ARG, "timing is on: a batch records the plan's launches");
+    }
+    // 1. record every plan's launch sequence with its dependency levels; the
+    //    plan's own pointer stands for the call's stream (never passed to CUDA)
+    Recorder rec;
+    for (int32_t i = 0; i < n; i++) {
+        cwt_plan* p = plans[i];
+        rec.stream_level.clear();
+        rec.event_level.clear();
+        set_rec(p, &rec);
+        cwt_status st = run_launches(p, signals_dev[i], W_dev[i], spectra_dev ? spectra_dev[i] : nullptr,
+                                     (cudaStream_t)(void*)p);
+        set_rec(p, nullptr);
+        if (st != CWT_OK) return st;
+    }
+    // 2. group by (level, grouped kernel)
+    std::map<std::pair<int, const void*>, std::vector<int>> by;
+    for (int i = 0; i < (int)rec.launches.size(); i++) {
+        const RecLaunch& r = rec.launches[i];
+        if ((int64_t)r.grid.x * r.grid.y * r.grid.z == 0) continue;
+        by[{r.level, r.gfn}].push_back(i);
+    }
+    cwt_batch* b = new (std::nothrow) cwt_batch();
+    if (!b) return CWT_ERR_OOM;
+    b->device = plans[0]->device;
+    b->n_streams = n_streams;
+    b->recorded = (int64_t)rec.launches.size();
+    std::vector<unsigned char> host;
+    auto take = [&](size_t bytes) {
+        const size_t off = align16(host.size());
+        host.resize(off + bytes, 0);
+        return off;
+    };
+    for (const auto& kv : by) {
+        const std::vector<int>& idx = kv.second;
+        const RecLaunch& r0 = rec.launches[idx[0]];
+        cwt_batch::Group g{};
+        g.gfn = r0.gfn;
+        g.block = r0.block;
+        g.level = r0.level;
+        g.stride = (int32_t)align16(r0.arg.size() * 4);
+        g.smem = 0;
+        for (int i : idx) {
+            const RecLaunch& r = rec.launches[i];
+            if (r.arg.size() != r0.arg.size() || r.block.x != r0.block.x || r.block.y != r0.block.y ||
+                r.block.z != r0.block.z || r.grid.z != 1) {
+                free_batch(b);
+                return fail(plans[0], CWT_ERR_INTERNAL, "inconsistent launches of one kernel");
+            }
+            g.smem = std::max(g.smem, r.smem);
+            g.ctas += (int64_t)r.grid.x * r.grid.y;
+        }
+        if (g.ctas > INT32_MAX) {
+            free_batch(b);
+            return fail(plans[0], CWT_ERR_UNSUPPORTED, "batch too large for one grouped launch");
+        }
+        g.args_off = take((size_t)g.stride * idx.size());
+        g.geom_off = take(sizeof(int2) * idx.size());
+        g.sub_off = take(sizeof(int32_t) * (size_t)g.ctas);
+        int32_t first = 0;
+        for (size_t k = 0; k < idx.size(); k++) {
+            const RecLaunch& r = rec.launches[idx[k]];
+            std::memcpy(host.data() + g.args_off + k * g.stride, r.arg.data(), r.arg.size() * 4);
+            const int2 geo = make_int2(first, (int)r.grid.x);
+            std::memcpy(host.data() + g.geom_off + k * sizeof(int2), &geo, sizeof(int2));
+            int32_t* sub = (int32_t*)(host.data() + g.sub_off);
+            const int32_t cnt = (int32_t)(r.grid.x * r.grid.y);
+            for (int32_t c = 0; c < cnt; c++) sub[first + c] = (int32_t)k;
+            first += cnt;
+        }
+        b->ctas += g.ctas;
+        b->groups.push_back(g);
+    }
+    // level index (std::map orders the groups by level)
+    const int nlev = b->groups.empty() ? 0 : b->groups.back().level + 1;
+    b->level_first.assign(nlev + 1, (int)b->groups.size());
+    for (int gi = (int)b->groups.size() - 1; gi >= 0; gi--) b->level_first[b->groups[gi].level] = gi;
+    for (int l = nlev - 1; l >= 0; l--) b->level_first[l] = std::min(b->level_first[l], b->level_first[l + 1]);
+    // 3. device tables, streams, shared-memory opt-in of the grouped kernels
+    cudaError_t e = cudaMalloc(&b->d_buf, std::max<size_t>(host.size(), 16));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_buf, host.data(), host.size(), cudaMemcpyHostToDevice);
+    for (int i = 1; i < n_streams && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && n_streams > 1) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : fail(plans[0], CWT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (const auto& g : b->groups) {
+        cwt_status st = opt_in_smem(plans[0], g.gfn);
+        if (st != CWT_OK) {
+            free_batch(b);
+            return st;
+        }
+    }
+    *batch = b;
+    return CWT_OK;
+}
+
+cwt_status cwt_batch_exec(cwt_batch* b, void* stream) {
+    if (!b) return CWT_ERR_INVALID_ARG;
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d != b->device) return CWT_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nlev = (int)b->level_first.size() - 1;
+    for (int l = 0; l < nlev; l++) {
+        const int g0 = b->level_first[l], g1 = b->level_first[l + 1];
+        const int k = std::min(b->n_streams, g1 - g0);
+        if (k > 1) {
+            if (cudaEventRecord(b->ev_fork, s) != cudaSuccess) return CWT_ERR_CUDA;
+            for (int j = 1; j < k; j++)
+                if (cudaStreamWaitEvent(b->side[j], b->ev_fork, 0) != cudaSuccess) return CWT_ERR_CUDA;
+        }
+        for (int gi = g0; gi < g1; gi++) {
+            const cwt_batch::Group& g = b->groups[gi];
+            GroupMap gm{b->d_buf + g.args_off, (const int32_t*)(b->d_buf + g.sub_off),
+                        (const int2*)(b->d_buf + g.geom_off), g.stride};
+            void* args[] = {&gm};
+            const int j = (gi - g0) % k;
+            if (cudaLaunchKernel(g.gfn, dim3((unsigned)g.ctas), g.block, args, g.smem, j ? b->side[j] : s) !=
+                cudaSuccess)
+                return CWT_ERR_CUDA;
+        }
+        for (int j = 1; j < k; j++) {
+            if (cudaEventRecord(b->ev_join[j], b->side[j]) != cudaSuccess) return CWT_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, b->ev_join[j], 0) != cudaSuccess) return CWT_ERR_CUDA;
+        }
+    }
+    return CWT_OK;
+}
+
+cwt_status cwt_batch_info(const cwt_batch* b, int32_t* n_levels, int32_t* n_launches, int64_t* n_ctas,
+                          int64_t* n_recorded) {
+    if (!b) return CWT_ERR_INVALID_ARG;
+    if (n_levels) *n_levels = (int32_t)b->level_first.size() - 1;
+    if (n_launches) *n_launches = (int32_t)b->groups.size();
+    if (n_ctas) *n_ctas = b->ctas;
+    if (n_recorded) *n_recorded = b->recorded;
+    return CWT_OK;
+}
+
+cwt_status cwt_batch_destroy(cwt_batch* b) {
+    if (b) cudaDeviceSynchronize();
+    free_batch(b);
     return CWT_OK;
 }
 

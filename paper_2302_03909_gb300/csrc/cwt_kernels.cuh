@@ -86,6 +86,54 @@ struct Params {
                              // truncation threshold for v^2 >= corr_v2
 };
 
+// Block coordinates of a CTA within its launch.  A plain launch takes them from
+// blockIdx and gridDim.  A grouped launch merges the launches of one kernel
+// made by several plans into one grid: each CTA then takes the coordinates it
+// has within the launch it came from (see group_args).
+struct Cta {
+    int x, y;   // blockIdx.x, blockIdx.y of the original launch
+    int nx;     // its gridDim.x
+};
+__device__ __forceinline__ Cta cta_plain() { return {(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
+
+// Grouped launch descriptor.  CTA b of the merged grid runs CTA (x, y) of
+// sub-launch i = cta_sub[b], where geom[i] = (first merged CTA of i, grid.x of
+// i) and x + nx y = b - first; the kernel argument of sub-launch i is the
+// struct at args + i * stride.  The sub-launches of one grouped launch are
+// independent of each other (no order among them is kept).
+struct GroupMap {
+    const unsigned char* args;
+    const int32_t* cta_sub;
+    const int2* geom;
+    int32_t stride;
+};
+
+// Copies this CTA's kernel argument into shared memory and returns it; sets c.
+// Every thread of the block must call it (it ends with a barrier).
+template <class A>
+__device__ __forceinline__ const A& group_args(const GroupMap& g, Cta& c) {
+    static_assert(sizeof(A) % 4 == 0, "argument structs are copied as 32-bit words");
+    __shared__ __align__(16) uint32_t sa[sizeof(A) / 4];
+    const int i = __ldg(&g.cta_sub[blockIdx.x]);
+    const int2 geo = __ldg(&g.geom[i]);
+    const int local = (int)blockIdx.x - geo.x;
+    c.x = local % geo.y;
+    c.y = local / geo.y;
+    c.nx = geo.y;
+    const uint32_t* src = (const uint32_t*)(g.args + (size_t)i * (size_t)g.stride);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
+    for (int w = tid; w < (int)(sizeof(A) / 4); w += nthr) sa[w] = __ldg(&src[w]);
+    __syncthreads();
+    return *reinterpret_cast<const A*>(sa);
+}
+
+// Pruned pass-1 launch argument (the pass-2 length L and the tiles per column)
+struct Wide1pArgs {
+    Params p;
+    int32_t L, tpb;
+    int32_t pad_[2];
+};
+
 // ------------------------------------------------------------------ helpers
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -552,9 +600,8 @@ struct BandFill {
 // One CTA handles D consecutive tiles of T columns of one job (D = p.D at
 // run time): the band values, the job descriptor and the power reduction are
 // paid once per CTA.
-template <int LOGL, int T, bool CROP, int RD = 1, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
-    k_band(Params p) {
+template <int LOGL, int T, bool CROP, int RD, int MAXLR>
+__device__ __forceinline__ void band_body(const Params& p, const Cta c) {
     constexpr int L = 1 << LOGL;
     constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
@@ -563,7 +610,7 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
     __shared__ double red[2 * ((NT + 31) / 32)];
     __shared__ Job sJ;
 
-    const int tile = blockIdx.x;
+    const int tile = c.x;
     if (threadIdx.x == 0) sJ = p.jobs[__ldg(&p.tile_job[tile])];
     __syncthreads();
     const Job& J = sJ;
@@ -583,13 +630,32 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
     write_partials<NT>(p, J, out, tile - J.tile0, red);
 }
 
+template <int LOGL, int T, bool CROP, int RD = 1, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
+    k_band(Params p) {
+    band_body<LOGL, T, CROP, RD, MAXLR>(p, cta_plain());
+}
+template <int LOGL, int T, bool CROP, int RD = 1, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
+    k_band_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    band_body<LOGL, T, CROP, RD, MAXLR>(p, c);
+}
+
 // The band values of every band job, once per call: grid = band jobs.
-static __global__ void __launch_bounds__(256) k_band_table(Params p) {
+__device__ __forceinline__ void band_table_body(const Params& p, const Cta c) {
     __shared__ Job sJ;
-    if (threadIdx.x == 0) sJ = p.jobs[blockIdx.x];
+    if (threadIdx.x == 0) sJ = p.jobs[c.x];
     __syncthreads();
     float2* zt = const_cast<float2*>(p.Zt) + sJ.zt_off;
     for (int i = threadIdx.x; i < sJ.K; i += 256) zt[i] = band_value(p, sJ, sJ.k_lo + i);
+}
+static __global__ void __launch_bounds__(256) k_band_table(Params p) { band_table_body(p, cta_plain()); }
+static __global__ void __launch_bounds__(256) k_band_table_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    band_table_body(p, c);
 }
 
 // ------------------------------------------------------------ wide pass 1
@@ -649,38 +715,48 @@ struct YOut {
 };
 
 // grid (L / T, jobs in batch): T columns b of the A-point DFTs of one job
-template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_wide1(Params p) {
+template <int LOGA, int T, int MAXLR>
+__device__ __forceinline__ void wide1_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
     __shared__ Job sJ;
-    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + c.y];
     __syncthreads();
-    const int b0 = blockIdx.x * T;
+    const int b0 = c.x * T;
     Wide1Fill fill{&p, &sJ, b0, L, 1 << LOGA};
-    YOut<true> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b0, 0, 1 << LOGA, 1};
+    YOut<true> out{&p, p.Y + (int64_t)c.y * p.M, b0, 0, 1 << LOGA, 1};
     cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
+}
+
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_wide1(Params p) {
+    wide1_body<LOGA, T, MAXLR>(p, cta_plain());
+}
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_wide1_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    wide1_body<LOGA, T, MAXLR>(p, c);
 }
 
 // Pruned pass 1: column b only holds the band bins k = b mod L, i.e. the
 // sub-band a in [a0, a0 + P_b) of the A-point problem (k = b + L a), so its
 // A-point DFT is itself a band tile of L1 >= P_b points over A1 = A / L1
 // columns d1 (d = d1 + A1 c1).  grid (L * tiles_per_b, jobs in batch).
-template <int LOGL1, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGL1, MAXLR), min_blocks(T * col_threads(LOGL1, MAXLR)))
-    k_wide1p(Params p, int L, int tiles_per_b) {
+template <int LOGL1, int T, int MAXLR>
+__device__ __forceinline__ void wide1p_body(const Params& p, const int L, const int tiles_per_b, const Cta c) {
     constexpr int L1 = 1 << LOGL1;
     constexpr int NT = T * col_threads(LOGL1, MAXLR);
     extern __shared__ float2 smem[];
     float2* Zs = smem;
     float2* buf = smem + L1;
     __shared__ Job sJ;
-    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + c.y];
     __syncthreads();
     const Job& J = sJ;
-    const int b = blockIdx.x / tiles_per_b;
-    const int d0 = (blockIdx.x - b * tiles_per_b) * T;
+    const int b = c.x / tiles_per_b;
+    const int d0 = (c.x - b * tiles_per_b) * T;
     const int A = p.M / L;
     const int A1 = A >> LOGL1;
     const int kb0 = J.k_lo + ((b - J.k_lo) & (L - 1));      // first band bin = b mod L
@@ -693,8 +769,21 @@ __global__ void __launch_bounds__(T * col_threads(LOGL1, MAXLR), min_blocks(T * 
     }
     __syncthreads();
     BandFill<LOGL1> fill{&p, Zs, a0, (uint32_t)L, d0};
-    YOut<false> out{&p, p.Y + (int64_t)blockIdx.y * p.M, b, d0, A, A1};
+    YOut<false> out{&p, p.Y + (int64_t)c.y * p.M, b, d0, A, A1};
     cta_fft<LOGL1, T, NT, false, MAXLR>(buf, p.tw_tab, fill, out, min(T, A1 - d0));
+}
+
+template <int LOGL1, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL1, MAXLR), min_blocks(T * col_threads(LOGL1, MAXLR)))
+    k_wide1p(Wide1pArgs a) {
+    wide1p_body<LOGL1, T, MAXLR>(a.p, a.L, a.tpb, cta_plain());
+}
+template <int LOGL1, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL1, MAXLR), min_blocks(T * col_threads(LOGL1, MAXLR)))
+    k_wide1p_g(GroupMap g) {
+    Cta c;
+    const Wide1pArgs& a = group_args<Wide1pArgs>(g, c);
+    wide1p_body<LOGL1, T, MAXLR>(a.p, a.L, a.tpb, c);
 }
 
 // ------------------------------------------------------------ wide pass 2
@@ -712,28 +801,40 @@ struct YFill {
 
 // grid (A / (T D), jobs in batch): D = p.D tiles of T columns d of the
 // L-point DFTs over b
-template <int LOGL, int T, bool CROP, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
-    k_wide2(Params p) {
+template <int LOGL, int T, bool CROP, int MAXLR>
+__device__ __forceinline__ void wide2_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     __shared__ double red[2 * ((NT + 31) / 32)];
     __shared__ Job sJ;
-    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + blockIdx.y];
+    if (threadIdx.x == 0) sJ = p.jobs[p.job0 + c.y];
     __syncthreads();
     const Job& J = sJ;
-    const int dbase = blockIdx.x * T * p.D;
+    const int dbase = c.x * T * p.D;
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
     for (int q = 0; q < p.D; q++) {
         const int d0 = dbase + q * T;
         if (d0 >= p.A) break;
         if (q > 0) __syncthreads();
-        YFill fill{p.Y + (int64_t)blockIdx.y * p.M, p.A, d0};
+        YFill fill{p.Y + (int64_t)c.y * p.M, p.A, d0};
         out.d0 = d0;
         cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
     }
-    write_partials<NT>(p, J, out, blockIdx.x, red);
+    write_partials<NT>(p, J, out, c.x, red);
+}
+
+template <int LOGL, int T, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
+    k_wide2(Params p) {
+    wide2_body<LOGL, T, CROP, MAXLR>(p, cta_plain());
+}
+template <int LOGL, int T, bool CROP, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR)))
+    k_wide2_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    wide2_body<LOGL, T, CROP, MAXLR>(p, c);
 }
 
 // ------------------------------------------------------------ forward
@@ -765,23 +866,33 @@ struct FOut {
 };
 
 // pass 1 of the forward: grid L / T, A-point DFTs of the columns b
-template <int LOGA, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_fwd1(Params p) {
+template <int LOGA, int T, int MAXLR>
+__device__ __forceinline__ void fwd1_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGA, MAXLR);
     extern __shared__ float2 smem[];
     const int L = p.M >> LOGA;
-    const int b0 = blockIdx.x * T;
+    const int b0 = c.x * T;
     SigFill fill{&p, b0, L};
     YOut<true> out{&p, p.Y, b0, 0, 1 << LOGA, 1};
     cta_fft<LOGA, T, NT, true, MAXLR>(smem, p.tw_tab, fill, out, min(T, L - b0));
 }
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_fwd1(Params p) {
+    fwd1_body<LOGA, T, MAXLR>(p, cta_plain());
+}
+template <int LOGA, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGA, MAXLR), min_blocks(T * col_threads(LOGA, MAXLR))) k_fwd1_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    fwd1_body<LOGA, T, MAXLR>(p, c);
+}
 
 // pass 2 of the forward (or the whole forward when A = 1): grid A / T
-template <int LOGL, int T, int MAXLR = 5>
-__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR))) k_fwd2(Params p) {
+template <int LOGL, int T, int MAXLR>
+__device__ __forceinline__ void fwd2_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
-    const int d0 = blockIdx.x * T;
+    const int d0 = c.x * T;
     FOut out{p.Fp_out, p.A, d0, p.M >> 1};
     if (p.A == 1) {
         SigFill fill{&p, 0, 1};
@@ -791,20 +902,47 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
         cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, min(T, p.A - d0));
     }
 }
+template <int LOGL, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR))) k_fwd2(Params p) {
+    fwd2_body<LOGL, T, MAXLR>(p, cta_plain());
+}
+template <int LOGL, int T, int MAXLR = 5>
+__global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * col_threads(LOGL, MAXLR))) k_fwd2_g(GroupMap g) {
+    Cta c;
+    const Params& p = group_args<Params>(g, c);
+    fwd2_body<LOGL, T, MAXLR>(p, c);
+}
 
 // ------------------------------------------------------------ power
 
 // spectrum[s] = (sum of the row's partials in fixed order) / N
-static __global__ void k_power_finalize(const double* __restrict__ partials, const int32_t* __restrict__ off,
-                                        const int32_t* __restrict__ cnt, int32_t S, int64_t N,
-                                        double* __restrict__ spectrum) {
-    int s = blockIdx.x;
+__device__ __forceinline__ void power_finalize_body(const double* __restrict__ partials, const int32_t* __restrict__ off,
+                                                    const int32_t* __restrict__ cnt, int32_t S, int64_t N,
+                                                    double* __restrict__ spectrum, int s) {
     if (s >= S || cnt[s] == 0) return;          // rows without partials belong to a child plan
     double acc = 0.0;
     for (int i = threadIdx.x; i < cnt[s]; i += 32) acc += partials[off[s] + i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (threadIdx.x == 0) spectrum[s] = acc / (double)N;
+}
+static __global__ void k_power_finalize(const double* __restrict__ partials, const int32_t* __restrict__ off,
+                                        const int32_t* __restrict__ cnt, int32_t S, int64_t N,
+                                        double* __restrict__ spectrum) {
+    power_finalize_body(partials, off, cnt, S, N, spectrum, blockIdx.x);
+}
+struct PowerArgs {
+    const double* partials;
+    const int32_t* off;
+    const int32_t* cnt;
+    double* spectrum;
+    int64_t N;
+    int32_t S, pad_;
+};
+static __global__ void k_power_finalize_g(GroupMap g) {
+    Cta c;
+    const PowerArgs& a = group_args<PowerArgs>(g, c);
+    power_finalize_body(a.partials, a.off, a.cnt, a.S, a.N, a.spectrum, c.x);
 }
 
 // spectrum[s] = (sum_c partials[s * chunks + c] in fixed order) / N

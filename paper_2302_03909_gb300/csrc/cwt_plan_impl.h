@@ -4,12 +4,50 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/cwt.h"
 #include "cwt_kernels.cuh"
+
+// Launch recording for batches (cwt_batch_create).  A plan whose rec is set
+// records each launch (the grouped form of its kernel, the launch shape and
+// the argument struct) instead of making it.  The level of a launch is its
+// depth in the plan's stream and event order: every launch a launch depends on
+// has a lower level, so running the levels one after another, each level's
+// launches in any order or at once, keeps every dependency.
+struct RecLaunch {
+    const void* gfn;
+    dim3 grid, block;
+    size_t smem;
+    int level;
+    std::vector<uint32_t> arg;
+};
+struct Recorder {
+    std::vector<RecLaunch> launches;
+    std::unordered_map<const void*, int> stream_level, event_level;
+    int level_of(const void* s) const {
+        auto it = stream_level.find(s);
+        return it == stream_level.end() ? 0 : it->second;
+    }
+    void add(cudaStream_t s, const void* gfn, dim3 grid, dim3 block, size_t smem, const void* arg, size_t bytes) {
+        const int l = level_of((const void*)s);
+        RecLaunch r{gfn, grid, block, smem, l, std::vector<uint32_t>((bytes + 3) / 4, 0u)};
+        std::memcpy(r.arg.data(), arg, bytes);
+        launches.push_back(std::move(r));
+        stream_level[(const void*)s] = l + 1;
+    }
+    void record(cudaEvent_t e, cudaStream_t s) { event_level[(const void*)e] = level_of((const void*)s); }
+    void wait(cudaStream_t s, cudaEvent_t e) {
+        auto it = event_level.find((const void*)e);
+        const int el = it == event_level.end() ? 0 : it->second;
+        stream_level[(const void*)s] = std::max(level_of((const void*)s), el);
+    }
+};
 
 struct cwt_plan {
     int64_t N = 0, M = 0;
@@ -102,6 +140,8 @@ struct cwt_plan {
     std::vector<int64_t> sub_E;
     int64_t ext_E = 0;                    // extension on each side of the shared buffer
     void* d_ext = nullptr;                // N + 2 ext_E samples, the input's dtype
+
+    Recorder* rec = nullptr;              // set while a batch records this plan's launches
 
     std::string err;
 };

@@ -11,7 +11,7 @@ static void fill(Tables& t, std::integer_sequence<int, L...>) {
 void fill_wide_tables(Tables& t) {
     fill(t, std::make_integer_sequence<int, kLmaxLog>{});
     // 8192-point columns: stages of radix <= 16 (1024 threads, 16 values each)
-    t.wide1[13] = {k_wide1<13, 1, 4>, 1, col_threads(13, 4), 13};
+    t.wide1[13] = {k_wide1<13, 1, 4>, k_wide1_g<13, 1, 4>, 1, col_threads(13, 4), 13};
     t.wide2[10][0] = wide2_entry<10, band_T(10), false>();
     t.wide2[10][1] = wide2_entry<10, band_T(10), true>();
     t.wide2[11][0] = wide2_entry<11, band_T(11), false>();

@@ -28,23 +28,25 @@ constexpr int p1var_T(int logl, int q) { return wide1p_T(logl) < (128 >> q) ? wi
 // direct depths of the L = 1024 band kernel (bands up to RD * 1024 bins)
 constexpr int kBandDepthLog = 10;
 
+// fn: the kernel; gfn: its grouped form (one launch over several plans' launches)
 using KernFn = void (*)(Params);
-struct Entry { KernFn fn; int T, NT, logl; };
-using KernFnP = void (*)(Params, int, int);
-struct EntryP { KernFnP fn; int T, NT, logl; };
+using KernFnG = void (*)(GroupMap);
+struct Entry { KernFn fn; KernFnG gfn; int T, NT, logl; };
+using KernFnP = void (*)(Wide1pArgs);
+struct EntryP { KernFnP fn; KernFnG gfn; int T, NT, logl; };
 
 template <int LOGL, int T, bool CROP, int RD = 1>
-Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, T, T * col_threads(LOGL), LOGL}; }
+Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, k_band_g<LOGL, T, CROP, RD>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry wide1_entry() { return {k_wide1<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
+Entry wide1_entry() { return {k_wide1<LOGL, T>, k_wide1_g<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T, bool CROP>
-Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, T, T * col_threads(LOGL), LOGL}; }
+Entry wide2_entry() { return {k_wide2<LOGL, T, CROP>, k_wide2_g<LOGL, T, CROP>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry fwd1_entry() { return {k_fwd1<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
+Entry fwd1_entry() { return {k_fwd1<LOGL, T>, k_fwd1_g<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-Entry fwd2_entry() { return {k_fwd2<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
+Entry fwd2_entry() { return {k_fwd2<LOGL, T>, k_fwd2_g<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 template <int LOGL, int T>
-EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
+EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, k_wide1p_g<LOGL, T>, T, T * col_threads(LOGL), LOGL}; }
 
 struct Tables {
     Entry band[kLmaxLog + 1][2];            // [log2 L][crop]
