@@ -72,7 +72,11 @@ typedef enum {
                                   Morlet only) the same result through zero-padded transforms of the
                                   periodically extended signal; scales whose spectrum is not negligible
                                   (1e-7) at the Nyquist frequency give CWT_ERR_UNSUPPORTED */
-    CWT_BOUNDARY_ZERO = 1      /* zero padding to M = next power of two >= 2N (Eq. 40 context) */
+    CWT_BOUNDARY_ZERO = 1      /* zero padding to M = next power of two >= 2N (Eq. 40 context).  With
+                                  fft_len 0, the same result with less padding where a scale's wavelet
+                                  is short: N a power of two, a periodic N-point transform plus an edge
+                                  correction; otherwise (GDW and Morlet) zero-padded transforms of
+                                  length M' >= N + E + 1, E the dilated wavelet's support */
 } cwt_boundary;
 
 typedef enum {
@@ -109,8 +113,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales,
 /* Frees the plan and its device memory (synchronises the device first).  NULL is OK. */
 cwt_status cwt_plan_destroy(cwt_plan* plan);
 
-/* M (the largest transform length for a periodic plan whose N is not a power
- * of two), the plan's device workspace in bytes, and whether W is complex
+/* M (the largest transform length for a plan whose N is not a power of two),
+ * the plan's device workspace in bytes, and whether W is complex
  * (1: interleaved complex64, Morlet; 0: float32, the real wavelets).  Any out-pointer may be NULL. */
 cwt_status cwt_plan_info(const cwt_plan* plan, int64_t* fft_len, size_t* workspace_bytes,
                          int32_t* out_is_complex);

@@ -346,6 +346,17 @@ double psi_support(int wavelet) { return wavelet == CWT_WAVELET_GDW ? 12.5 : 8.5
 
 int64_t edge_width(int wavelet, double wt) { return (int64_t)std::ceil(psi_support(wavelet) / wt) + 1; }
 
+// The scale's spectrum is negligible (1e-7 of its peak) at the Nyquist frequency.
+// Only then is the sampled wavelet the short one of support edge_width: a
+// spectrum cut off at the Nyquist frequency rings, and the transform then
+// depends on the padded length itself.
+bool nyquist_clear(int wavelet, double omega0, double wt) {
+    double u_lo, u_hi;
+    wavelet_band(wavelet, omega0, 1e-7, &u_lo, &u_hi);
+    const double nyq = kPi / wt;
+    return u_hi < nyq && u_lo > -nyq;
+}
+
 // psi(x) of Table 2 (GDW, Morlet), FP64
 void psi_x(int wavelet, double omega0, double x, double* re, double* im) {
     if (wavelet == CWT_WAVELET_GDW) {
@@ -603,10 +614,11 @@ cwt_status build_plan(cwt_plan* p) {
             Job J = wide[i];
             // pass 1 of column b has at most ceil(K / L) band bins: a pruned band tile of
             // L1 = 2^ceil(log2) points over A1 = A / L1 columns d1, with the widest
-            // column-count variant that fits A1; the whole A-point DFT when L1 = A
+            // column-count variant that fits A1; the whole A-point DFT when L1 = A, and
+            // for A <= 128, where the pruned tiles would be CTAs of a few threads
             int l1 = std::max(1, ilog2(((int64_t)J.K + L - 1) / L));
             int var = -1;
-            if (l1 <= kLmaxLog - 2 && l1 < p->wide_loga) {
+            if (p->wide_loga >= 8 && l1 <= kLmaxLog - 2 && l1 < p->wide_loga) {
                 const int64_t A1 = int64_t(1) << (p->wide_loga - l1);
                 for (int q = 0; q < kP1Var && var < 0; q++)
                     if (tb.wide1p[l1][q].T <= A1) var = q;
@@ -842,11 +854,12 @@ cwt_status check_device(cwt_plan* p) {
 cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     const Tables& tb = tables();
     cwt_status st;
-    if (!p->subs.empty()) {                      // periodic, N not a power of two
+    if (!p->subs.empty()) {                      // N not a power of two: sub-plans by padded length
         const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
         const size_t se = f64 ? sizeof(double) : sizeof(float);
         const size_t we = p->wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
-        {
+        const bool ext = p->boundary == CWT_BOUNDARY_PERIODIC;   // zero boundary: the signal itself
+        if (ext) {
             LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
             const int64_t total = p->N + 2 * p->ext_E;
             const unsigned blocks = (unsigned)std::min<int64_t>(4096, (total + 255) / 256);
@@ -860,7 +873,8 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             }
         }
         for (size_t i = 0; i < p->subs.size(); i++) {
-            const void* sig = (const char*)p->d_ext + (size_t)(p->ext_E - p->sub_E[i]) * se;
+            const void* sig = ext ? (const void*)((const char*)p->d_ext + (size_t)(p->ext_E - p->sub_E[i]) * se)
+                                  : signal;
             void* Wi = (char*)W + (size_t)p->sub_r0[i] * (size_t)p->N * we;
             double* spi = spectrum ? spectrum + p->sub_r0[i] : nullptr;
             if ((st = run_launches(p->subs[i], sig, Wi, spi, s)) != CWT_OK) return st;
@@ -1247,6 +1261,65 @@ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 }  // namespace
 
+// Zero boundary with N not a power of two (GDW, Morlet).  The zero-padded
+// transform restricted to n < N is the linear convolution of f with the
+// dilated wavelet; with M' >= N + E + 1 points (E: the support of the dilated
+// wavelet, beyond which it is negligible) no output n < N sees a wrapped term,
+// so a scale gives the same W with any such M' as with the default M (the
+// power of two >= 2N).  Consecutive rows sharing the power-of-two length
+// M' = min(M, pow2 >= N + E + 1) form zero-boundary sub-plans of fft_len M'.
+// *plan stays NULL (and CWT_OK is returned) when every row needs the default M.
+cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
+                             const cwt_plan_opts& o) {
+    *plan = nullptr;
+    const int64_t Mdef = int64_t(1) << ilog2(2 * N);
+    std::vector<double> wt(n_scales);
+    std::vector<int64_t> Mr(n_scales);
+    bool shorter = false;
+    for (int32_t i = 0; i < n_scales; i++) {
+        wt[i] = o.scale_unit == CWT_SCALE_DILATION ? 1.0 / scales[i] : scales[i];
+        const int64_t E = edge_width(wavelet, wt[i]);
+        Mr[i] = nyquist_clear(wavelet, o.omega0, wt[i]) ? std::min(Mdef, int64_t(1) << ilog2(N + E + 1)) : Mdef;
+        shorter |= Mr[i] < Mdef;
+    }
+    if (!shorter || Mdef > (int64_t(1) << kMaxLogM)) return CWT_OK;
+    cwt_plan* p = new (std::nothrow) cwt_plan();
+    if (!p) return CWT_ERR_OOM;
+    p->N = N;
+    p->out_len = N;
+    p->S = n_scales;
+    p->wavelet = wavelet;
+    p->boundary = CWT_BOUNDARY_ZERO;
+    p->opts = o;
+    p->w_tilde = wt;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        free_plan(p);
+        return CWT_ERR_CUDA;
+    }
+    for (int32_t r0 = 0; r0 < n_scales;) {
+        int32_t r1 = r0 + 1;
+        while (r1 < n_scales && Mr[r1] == Mr[r0]) r1++;
+        cwt_plan_opts so = o;
+        so.scale_unit = CWT_SCALE_W_TILDE;
+        so.fft_len = Mr[r0];
+        cwt_plan* sub = nullptr;
+        cwt_status st = cwt_plan_create_ex(&sub, N, wt.data() + r0, r1 - r0, wavelet, CWT_BOUNDARY_ZERO, &so);
+        if (st != CWT_OK) {
+            free_plan(p);
+            return st;
+        }
+        p->subs.push_back(sub);
+        p->sub_r0.push_back(r0);
+        p->sub_E.push_back(0);
+        p->ws_bytes += sub->ws_bytes;
+        p->M = std::max(p->M, Mr[r0]);
+        r0 = r1;
+    }
+    p->logM = ilog2(p->M);
+    *plan = p;
+    return CWT_OK;
+}
+
 // ====================================================================== ABI
 
 extern "C" {
@@ -1299,6 +1372,10 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
             M = o.fft_len;
         } else {
             M = int64_t(1) << ilog2(2 * N);
+            if (!is_pow2(N) && (wavelet == CWT_WAVELET_GDW || wavelet == CWT_WAVELET_MORLET)) {
+                cwt_status st = create_zero_split(plan, N, scales, n_scales, wavelet, o);
+                if (st != CWT_OK || *plan) return st;
+            }
         }
     }
     if (M < 2 || M > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
@@ -1330,7 +1407,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         int r0 = -1, r1 = -1;
         bool contiguous = true;
         for (int32_t i = 0; i < n_scales; i++) {
-            if (edge_width(wavelet, p->w_tilde[i]) > emax) continue;
+            if (edge_width(wavelet, p->w_tilde[i]) > emax || !nyquist_clear(wavelet, o.omega0, p->w_tilde[i]))
+                continue;
             if (r0 < 0) r0 = i;
             else if (r1 != i) contiguous = false;
             r1 = i + 1;

@@ -106,7 +106,11 @@ def test_small_parity(env, N, boundary, wavelet, smin, smax, S, kw):
     f = synth.lognormal_field(N, seed=N + S)
     sc = synth.log_scales(smin, smax, S)
     W, spec, M = run_gpu(env, f, sc, wavelet, boundary, **kw)
-    ref = orc.cwt_fft(f32(f), sc, wavelet, M=M, omega0=kw.get("omega0", 6.0), dx=kw.get("dx", 1.0))
+    # the paper's zero boundary: padding to the power of two >= 2N unless fft_len says otherwise
+    # (the plan itself may pad less where the wavelet is short)
+    M_ref = N if boundary == "periodic" else (kw.get("fft_len") or 1 << int(np.ceil(np.log2(2 * N))))
+    assert M <= M_ref
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=M_ref, omega0=kw.get("omega0", 6.0), dx=kw.get("dx", 1.0))
     assert rel_l2(W, ref) <= TOL
     # each row on its own, so a wrong scale cannot hide behind a large one
     for s in range(S):
@@ -335,3 +339,36 @@ def test_maximum_sizes_sampled(env, N, boundary, wavelet, smin, smax, S):
     assert np.max(np.abs(spec.cpu().numpy() - P) / P) < 1e-5
     del W, spec, P_dev
     plan.close()
+
+
+@pytest.mark.parametrize("N,wavelet,smin,smax,S,order,dtype", [
+    (1000, "gdw", 2.0, 250.0, 9, "asc", "f32"),
+    (3001, "morlet", 4.0, 1500.0, 10, "desc", "f32"),       # scales beyond N/4: some rows need 2N
+    (20011, "morlet", 4.0, 5000.0, 12, "shuffled", "f32"),  # prime N, rows in no order
+    (40000, "gdw", 2.0, 10000.0, 14, "asc", "f64"),          # wide two-pass scales in the sub-plans
+    (70000, "morlet", 4.0, 17500.0, 8, "asc", "f32"),
+])
+def test_zero_boundary_any_length(env, N, wavelet, smin, smax, S, order, dtype):
+    """Zero boundary with N not a power of two: rows whose wavelet is short run
+    as zero-boundary sub-plans padded to M' >= N + E + 1 only.  W and the power
+    spectrum must equal the oracle's FFTCWT with the paper's padding to the
+    power of two >= 2N."""
+    _, _, orc = env
+    f = synth.lognormal_field(N, seed=N + 5)
+    sc = synth.log_scales(smin, smax, S)
+    if order == "desc":
+        sc = sc[::-1].copy()
+    elif order == "shuffled":
+        sc = sc[np.random.default_rng(3).permutation(S)]
+    W, spec, M = run_gpu(env, f, sc, wavelet, "zero", dtype=dtype)
+    M_ref = 1 << int(np.ceil(np.log2(2 * N)))
+    assert M <= M_ref
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=M_ref)
+    assert rel_l2(W, ref) <= TOL
+    for s in range(S):
+        assert np.linalg.norm(W[s] - ref[s]) / np.linalg.norm(ref[s]) <= 10 * TOL, s
+        e = min(N // 8, 64)                               # both ends, where a wrapped term would land
+        edge = np.r_[0:e, N - e:N]
+        assert np.linalg.norm(W[s, edge] - ref[s, edge]) <= 10 * TOL * np.linalg.norm(ref[s]) + 1e-12, s
+    P = orc.wavelet_power(ref)
+    assert np.max(np.abs(spec - P) / P) < 1e-4
