@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--workload", default="lognormal_n1m_morlet_s64", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch shape instead of the plan-time tuning (cwt_plan_opts.tune)")
     ap.add_argument("--no-fft-baseline", action="store_true",
                     help="skip the comparison with the library FFT (torch.fft / cuFFT) written the usual way")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -509,7 +511,10 @@ def run_ours(args):
     f = rank_signal(args.workload, rank, world)
     bounds, sc, subset = workload_subset(args)
     N, S = len(f), len(sc)
-    plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b) for b in bounds]
+    t_plan0 = time.perf_counter()
+    plans = [cwt.cwt_plan_create(N, sc, w["wavelet"], b, tune=not args.no_tune) for b in bounds]
+    t_plan = time.perf_counter() - t_plan0
+    shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes")} for p in plans]
     sig = torch.tensor(f, dtype=torch.float32, device=dev)
     outs = [(p.empty_output(dev), torch.empty(S, dtype=torch.float64, device=dev)) for p in plans]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -612,6 +617,7 @@ def run_ours(args):
                        "fft_len": [p.M for p in plans], "power_spectrum": True,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "inputs": "resident in HBM", "parallelism": f"replicas x{world}",
+                       "launch_shape": shapes, "plan_s": round(t_plan, 3),
                        **({"subset": subset} if subset else {})},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,

@@ -97,6 +97,14 @@ typedef struct {
                             paper's padding N + 2 Nint(chi / w~_min), rounded up). */
     double eps_trunc;    /* spectral bins where |psi_hat| < eps_trunc * max|psi_hat| are
                             skipped (default 1e-10; 0 keeps every bin) */
+    int32_t min_ctas;    /* launch shape: the W-writing launches take up to 8 tiles per CTA while
+                            keeping at least this many CTAs (0: 304, two per SM; at most 2^20) */
+    int32_t tune;        /* 1: at creation, time plans with min_ctas in {152, 304, 608} and
+                            wide_batch_bytes in {16, 32} MiB (a nonzero value given above is kept)
+                            on this device and keep the fastest.  Needs temporary device memory of
+                            the output's size and runs the transform a few times. 0: no tuning */
+    int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
+                            (0: 32 MiB; at most 2^36) */
 } cwt_plan_opts;
 
 void cwt_plan_opts_default(cwt_plan_opts* opts);
@@ -110,6 +118,9 @@ cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int
 cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales,
                               int32_t n_scales, int32_t wavelet, int32_t boundary,
                               const cwt_plan_opts* opts);
+/* The options a plan was made with, min_ctas and wide_batch_bytes as used
+ * (after defaults and tuning). */
+cwt_status cwt_plan_get_opts(const cwt_plan* plan, cwt_plan_opts* opts);
 /* Frees the plan and its device memory (synchronises the device first).  NULL is OK. */
 cwt_status cwt_plan_destroy(cwt_plan* plan);
 

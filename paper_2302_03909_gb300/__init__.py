@@ -24,7 +24,7 @@ __all__ = [
     "cwt_exec_with_power", "cwt_wavelet_power", "cwt_env_power", "cwt_icwt", "cwt_exec_host",
     "cwt_scales_paper_grid",
     "cwt_status_string", "cwt_wavelet_power_noalloc", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
-    "Batch", "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy",
+    "Batch", "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy", "cwt_plan_get_opts",
     "ABI_FUNCTIONS", "KERNEL_CLASSES",
 ]
 
@@ -39,7 +39,7 @@ ABI_FUNCTIONS = [
     "cwt_plan_info", "cwt_exec", "cwt_exec_with_power", "cwt_wavelet_power", "cwt_exec_host",
     "cwt_scales_paper_grid", "cwt_status_string", "cwt_plan_last_error", "cwt_plan_set_timing",
     "cwt_plan_get_timing", "cwt_wavelet_power_noalloc", "cwt_env_power", "cwt_icwt",
-    "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy",
+    "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy", "cwt_plan_get_opts",
 ]
 NOALLOC_MAX_PARTIALS = 65536
 NOALLOC_CHUNK = 32768
@@ -49,7 +49,9 @@ KERNEL_CLASSES = {"forward": 0, "band": 1, "wide1": 2, "wide2": 3, "power": 4}
 class _Opts(ctypes.Structure):
     _fields_ = [("omega0", ctypes.c_double), ("dx", ctypes.c_double),
                 ("scale_unit", ctypes.c_int32), ("input_dtype", ctypes.c_int32),
-                ("fft_len", ctypes.c_int64), ("eps_trunc", ctypes.c_double)]
+                ("fft_len", ctypes.c_int64), ("eps_trunc", ctypes.c_double),
+                ("min_ctas", ctypes.c_int32), ("tune", ctypes.c_int32),
+                ("wide_batch_bytes", ctypes.c_int64)]
 
 
 class CwtError(RuntimeError):
@@ -118,6 +120,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
                                        ctypes.POINTER(i64)]
         lib.cwt_batch_destroy.restype = ctypes.c_int
         lib.cwt_batch_destroy.argtypes = [vp]
+        lib.cwt_plan_get_opts.restype = ctypes.c_int
+        lib.cwt_plan_get_opts.argtypes = [vp, ctypes.POINTER(_Opts)]
         _lib = lib
         return lib
 
@@ -186,7 +190,8 @@ class Plan:
 
 def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "periodic", *,
                     omega0: float = 6.0, dx: float = 1.0, scale_unit: str = "dilation",
-                    input_dtype: str = "f32", fft_len: int = 0, eps_trunc: float = 1e-10) -> Plan:
+                    input_dtype: str = "f32", fft_len: int = 0, eps_trunc: float = 1e-10,
+                    min_ctas: int = 0, tune: bool = False, wide_batch_bytes: int = 0) -> Plan:
     lib = load_library()
     sc = np.ascontiguousarray(scales, dtype=np.float64)
     opts = _Opts()
@@ -196,6 +201,9 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     opts.input_dtype = INPUT_DTYPES[input_dtype]
     opts.fft_len = int(fft_len)
     opts.eps_trunc = float(eps_trunc)
+    opts.min_ctas = int(min_ctas)
+    opts.tune = 1 if tune else 0
+    opts.wide_batch_bytes = int(wide_batch_bytes)
     h = ctypes.c_void_p()
     st = lib.cwt_plan_create_ex(ctypes.byref(h), int(N),
                                 sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sc),
@@ -204,6 +212,13 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     return Plan(h, int(N), len(sc), wavelet, boundary,
                 dict(omega0=omega0, dx=dx, scale_unit=scale_unit, input_dtype=input_dtype,
                      fft_len=fft_len, eps_trunc=eps_trunc))
+
+
+def cwt_plan_get_opts(plan: Plan) -> dict:
+    """The options the plan was made with (launch shape as used, after tuning)."""
+    o = _Opts()
+    _check(load_library().cwt_plan_get_opts(plan._h, ctypes.byref(o)), plan)
+    return {name: getattr(o, name) for name, _ in _Opts._fields_}
 
 
 def cwt_plan_destroy(plan: Plan):

@@ -37,8 +37,8 @@ constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide 
 // are paid once per CTA), at most kMaxD
 constexpr int kMaxD = 8;
 constexpr int kMinCtas = 152 * 2;
-int pick_D(int64_t tiles_total) {
-    int64_t d = tiles_total / kMinCtas;
+int pick_D(int64_t tiles_total, int min_ctas) {
+    int64_t d = tiles_total / min_ctas;
     return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxD, d));
 }
 
@@ -582,7 +582,7 @@ cwt_status build_plan(cwt_plan* p) {
         const int64_t A = M >> ll;
         const int T = tb.band[ll][0].T;
         const int64_t tiles_job = (A + T - 1) / T;
-        const int D = pick_D(tiles_job * (int64_t)by_logl[slot].size());
+        const int D = pick_D(tiles_job * (int64_t)by_logl[slot].size(), p->opts.min_ctas);
         const int per_job = (int)((tiles_job + D - 1) / D);
         g.D = D;
         g.ntiles = 0;
@@ -605,9 +605,9 @@ cwt_status build_plan(cwt_plan* p) {
     if (!wide.empty()) {
         const int64_t A = M >> p->wide_logl;
         const int T2 = tb.wide2[p->wide_logl][0].T;
-        p->wide_G = (int)std::max<int64_t>(1, (int64_t)(kWideBatchBytes / ((size_t)M * sizeof(float2))));
+        p->wide_G = (int)std::max<int64_t>(1, p->opts.wide_batch_bytes / (int64_t)((size_t)M * sizeof(float2)));
         const int64_t tiles_job = (A + T2 - 1) / T2;
-        p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
+        p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()), p->opts.min_ctas);
         const int ntiles2 = (int)((tiles_job + p->wide_D - 1) / p->wide_D);
         const int L = 1 << p->wide_logl;
         for (size_t i = 0; i < wide.size(); i++) {
@@ -1320,6 +1320,91 @@ cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, i
     return CWT_OK;
 }
 
+// Plan-time tuning (opts.tune = 1): plans with the candidate launch-shape
+// options (the CTA target of the W-writing launches and the intermediate size
+// of a wide-scale launch; a value the caller fixed is kept) are created and
+// timed on this device, running the transform with power on a zero signal
+// into temporary buffers of the output's size (the kernels' work does not
+// depend on the values); the fastest plan is kept and the others destroyed.
+cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
+                        int32_t boundary, const cwt_plan_opts& o) {
+    struct Cand { int32_t ctas; int64_t wb; };
+    std::vector<Cand> cands;
+    for (int32_t c : {152 * 2, 152, 152 * 4})
+        for (int64_t wb : {int64_t(32) << 20, int64_t(16) << 20}) {
+            const Cand k{o.min_ctas ? o.min_ctas : c, o.wide_batch_bytes ? o.wide_batch_bytes : wb};
+            bool dup = false;
+            for (const Cand& q : cands) dup |= q.ctas == k.ctas && q.wb == k.wb;
+            if (!dup) cands.push_back(k);
+        }
+    cwt_plan* best = nullptr;
+    float best_ms = 0.f;
+    void* sig = nullptr;
+    void* W = nullptr;
+    double* sp = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cwt_status rc = CWT_OK;
+    auto cuda_ok = [&](cudaError_t e) {
+        if (e == cudaSuccess) return true;
+        cudaGetLastError();
+        rc = e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : CWT_ERR_CUDA;
+        return false;
+    };
+    for (const Cand& c : cands) {
+        cwt_plan_opts oc = o;
+        oc.tune = 0;
+        oc.min_ctas = c.ctas;
+        oc.wide_batch_bytes = c.wb;
+        cwt_plan* q = nullptr;
+        if ((rc = cwt_plan_create_ex(&q, N, scales, n_scales, wavelet, boundary, &oc)) != CWT_OK) break;
+        if (!sig) {
+            const size_t se = o.input_dtype == CWT_INPUT_F64 ? sizeof(double) : sizeof(float);
+            const size_t we = wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
+            if (!cuda_ok(cudaMalloc(&sig, (size_t)N * se)) || !cuda_ok(cudaMemset(sig, 0, (size_t)N * se)) ||
+                !cuda_ok(cudaMalloc(&W, (size_t)n_scales * (size_t)N * we)) ||
+                !cuda_ok(cudaMalloc(&sp, (size_t)n_scales * sizeof(double))) ||
+                !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) || !cuda_ok(cudaEventCreate(&e0)) ||
+                !cuda_ok(cudaEventCreate(&e1))) {
+                free_plan(q);
+                break;
+            }
+        }
+        float ms = 0.f;
+        for (int i = 0; i < 3 && rc == CWT_OK; i++) rc = cwt_exec_with_power(q, sig, W, sp, st);
+        if (rc == CWT_OK && cuda_ok(cudaEventRecord(e0, st))) {
+            for (int i = 0; i < 5 && rc == CWT_OK; i++) rc = cwt_exec_with_power(q, sig, W, sp, st);
+            if (rc == CWT_OK && cuda_ok(cudaEventRecord(e1, st)) && cuda_ok(cudaEventSynchronize(e1)))
+                cuda_ok(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (rc != CWT_OK) {
+            free_plan(q);
+            break;
+        }
+        if (!best || ms < best_ms) {
+            if (best) free_plan(best);
+            best = q;
+            best_ms = ms;
+        } else {
+            free_plan(q);
+        }
+    }
+    if (st) cudaStreamSynchronize(st);
+    if (sig) cudaFree(sig);
+    if (W) cudaFree(W);
+    if (sp) cudaFree(sp);
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != CWT_OK) {
+        if (best) free_plan(best);
+        return rc;
+    }
+    best->opts.tune = 1;
+    *plan = best;
+    return CWT_OK;
+}
+
 // ====================================================================== ABI
 
 extern "C" {
@@ -1332,6 +1417,9 @@ void cwt_plan_opts_default(cwt_plan_opts* o) {
     o->input_dtype = CWT_INPUT_F32;
     o->fft_len = 0;
     o->eps_trunc = 1e-10;
+    o->min_ctas = 0;
+    o->tune = 0;
+    o->wide_batch_bytes = 0;
 }
 
 cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
@@ -1359,6 +1447,12 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     if (wavelet == CWT_WAVELET_MORLET && !(o.omega0 > 0.0)) return CWT_ERR_INVALID_ARG;
     for (int32_t i = 0; i < n_scales; i++)
         if (!std::isfinite(scales[i]) || !(scales[i] > 0.0)) return CWT_ERR_INVALID_ARG;
+    if (o.min_ctas < 0 || o.min_ctas > (1 << 20) || o.wide_batch_bytes < 0 ||
+        o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1))
+        return CWT_ERR_INVALID_ARG;
+    if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
+    if (o.min_ctas == 0) o.min_ctas = kMinCtas;
+    if (o.wide_batch_bytes == 0) o.wide_batch_bytes = (int64_t)kWideBatchBytes;
 
     int64_t M;
     if (boundary == CWT_BOUNDARY_PERIODIC) {
@@ -1757,6 +1851,12 @@ cwt_status cwt_batch_info(const cwt_batch* b, int32_t* n_levels, int32_t* n_laun
 cwt_status cwt_batch_destroy(cwt_batch* b) {
     if (b) cudaDeviceSynchronize();
     free_batch(b);
+    return CWT_OK;
+}
+
+cwt_status cwt_plan_get_opts(const cwt_plan* plan, cwt_plan_opts* opts) {
+    if (!plan || !opts) return CWT_ERR_INVALID_ARG;
+    *opts = plan->opts;
     return CWT_OK;
 }
 

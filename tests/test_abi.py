@@ -72,6 +72,8 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=64, scales=[2.0], boundary="zero", fft_len=96), 2),   # not 2^k
     (dict(N=64, scales=[2.0], boundary="periodic", fft_len=128), 1),
     (dict(N=1 << 26, scales=[2.0], boundary="zero"), 2),          # M > 2^25
+    (dict(N=64, scales=[2.0], min_ctas=-1), 1),
+    (dict(N=64, scales=[2.0], wide_batch_bytes=-5), 1),
 ])
 def test_plan_argument_checks(cwt, kwargs, status):
     kw = dict(kwargs)

@@ -372,3 +372,37 @@ def test_zero_boundary_any_length(env, N, wavelet, smin, smax, S, order, dtype):
         assert np.linalg.norm(W[s, edge] - ref[s, edge]) <= 10 * TOL * np.linalg.norm(ref[s]) + 1e-12, s
     P = orc.wavelet_power(ref)
     assert np.max(np.abs(spec - P) / P) < 1e-4
+
+
+@pytest.mark.parametrize("boundary", ["periodic", "zero"])
+def test_tuned_plan_equals_default(env, boundary):
+    """A plan tuned at creation (launch shape measured on the device) computes
+    every output with the same arithmetic as the default plan: W is bitwise
+    equal; the power spectrum sums the same terms in another grouping (each
+    thread's FP32 partial runs over its CTA's tiles).  The N = 2^20 Morlet
+    workload, as the benchmark runs it."""
+    torch, cwt, _ = env
+    name = "lognormal_n1m_morlet_s64"
+    f = synth.workload_signal(name)
+    sc = synth.workload_scales(name)
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary)
+    p1 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, tune=True)
+    o0, o1 = cwt.cwt_plan_get_opts(p0), cwt.cwt_plan_get_opts(p1)
+    assert o0["tune"] == 0 and o0["min_ctas"] == 304 and o0["wide_batch_bytes"] == 32 << 20
+    assert o1["tune"] == 1 and o1["min_ctas"] in (152, 304, 608)
+    assert o1["wide_batch_bytes"] in (16 << 20, 32 << 20)
+    W0, s0 = cwt.cwt_exec_with_power(p0, sig)
+    W1, s1 = cwt.cwt_exec_with_power(p1, sig)
+    torch.cuda.synchronize()
+    assert torch.equal(W0, W1)
+    assert torch.allclose(s0, s1, rtol=1e-5, atol=0)
+    # every launch shape gives the same W
+    for mc, wb in [(152, 16 << 20), (608, 32 << 20), (1, 1 << 20)]:
+        p2 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, min_ctas=mc, wide_batch_bytes=wb)
+        W2 = cwt.cwt_exec(p2, sig)
+        torch.cuda.synchronize()
+        assert torch.equal(W0, W2), (mc, wb)
+        p2.close()
+    p0.close()
+    p1.close()
