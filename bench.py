@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--batch", action="store_true", help="measure a batch of uneven-length signals")
     ap.add_argument("--batch-signals", type=int, default=512, help="batch: number of signals")
     ap.add_argument("--batch-streams", type=int, default=16, help="batch: streams the graph spreads the signals over")
+    ap.add_argument("--batch-min-ctas", type=int, default=1,
+                    help="batch: the plans' min_ctas option (1: up to 8 tiles per CTA)")
     ap.add_argument("--batch-streams-grouped", type=int, default=4,
                     help="batch: streams a level of the batch API's grouped launches is spread over")
     return ap.parse_args()
@@ -421,7 +423,9 @@ def run_batch(args):
     import paper_2302_03909_gb300 as cwt
     # plans (one per signal) and resident device buffers, before any timing
     t0 = time.perf_counter()
-    plans = [cwt.cwt_plan_create(r.N, np.asarray(r.scales), r.wavelet, r.boundary) for r in reqs]
+    # plans for a batch take the fewest, largest CTAs: the batch supplies the parallelism
+    plans = [cwt.cwt_plan_create(r.N, np.asarray(r.scales), r.wavelet, r.boundary, min_ctas=args.batch_min_ctas)
+             for r in reqs]
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
     items = []
@@ -478,7 +482,7 @@ def run_batch(args):
                        "scale_samples": units, "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],
                        "streams": args.batch_streams, "inputs": "resident in HBM",
                        "plans": "one per signal, created before the timed runs",
-                       "grouped_streams": args.batch_streams_grouped,
+                       "grouped_streams": args.batch_streams_grouped, "plan_min_ctas": args.batch_min_ctas,
                        "timed": "value: the batch API (cwt_batch_exec, launches merged by kernel and level); "
                                 "graph: one CUDA graph over the per-signal launch sequences; one_by_one: one "
                                 "launch sequence per signal on one stream"},

@@ -268,7 +268,9 @@ cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, int32_t n_sca
  * streams a level's grouped launches are spread over.  The batch holds device
  * tables of about 4 bytes per CTA plus the launch arguments; the plans and
  * buffers stay owned by the caller and must outlive the batch, and a plan must
- * not run elsewhere while its batch runs.
+ * not run elsewhere while its batch runs.  Plans made for a batch do best
+ * with min_ctas = 1 (fewest, largest CTAs: the batch supplies the parallelism
+ * that a single plan's launches otherwise need).
  *
  * cwt_batch_exec runs the levels in order on `stream` (asynchronous; the
  * groups of a level fork to the batch's own streams and join back).
