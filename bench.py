@@ -106,17 +106,21 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(kernel: str, workload: str):
+def load_traffic(kernel: str, workload: str, alg_bytes_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, if one exists for
-    this kernel class and workload (profiles/traffic.txt: kernel workload bytes)."""
+    this kernel class and workload (profiles/traffic.txt: kernel, workload, DRAM
+    bytes per launch and algorithmic bytes per launch of the profiled launches),
+    scaled to this run's launches by their algorithmic bytes (the launch size
+    depends on the plan's launch shape; the traffic grows with the jobs a launch
+    takes)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         for line in fh:
             parts = line.split()
-            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
-                return float(parts[2])
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload:
+                return float(parts[2]) * alg_bytes_per_launch / float(parts[3])
     return None
 
 
@@ -575,7 +579,8 @@ def run_ours(args):
     dom = max([k for k in ("wide2", "band") if k in cls_tot] or list(cls_tot), key=lambda k: cls_tot[k][0])
     peak, peak_src = load_peaks()
     achieved = cls_tot[dom][2] / (cls_tot[dom][0] * 1e-3) / 1e9 if cls_tot[dom][0] > 0 else 0.0
-    traffic = load_traffic(dom, args.workload) if not subset else None
+    traffic = (load_traffic(dom, args.workload, cls_tot[dom][2] / max(1, cls_tot[dom][1]))
+               if not subset else None)
     units_per_step = S * N * len(plans)
     value = weak_scaling_value(units_per_step, args.steps, world, total_ms)
 
