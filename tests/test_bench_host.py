@@ -1,0 +1,23 @@
+"""Host-side pieces of bench.py that need no GPU."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+
+
+def test_traffic_scales_with_the_launch_size():
+    """The profiled DRAM bytes per pass-2 launch apply to launches of the same
+    algorithmic size; a launch with half the jobs is charged half."""
+    full = bench.load_traffic("wide2", "lognormal_n1m_morlet_s64", 26.0e6)
+    half = bench.load_traffic("wide2", "lognormal_n1m_morlet_s64", 13.0e6)
+    assert full is not None and abs(full - 28.8e6) < 1.0
+    assert abs(half - full / 2) < 1.0
+    assert bench.load_traffic("band", "lognormal_n1m_morlet_s64", 1.0) is None
+    assert bench.load_traffic("wide2", "no_such_workload", 1.0) is None
+
+
+def test_weak_scaling_value_counts_all_ranks():
+    # 4 steps of 1000 units on each of 2 ranks in 8 ms (max over ranks)
+    assert abs(bench.weak_scaling_value(1000.0, 4, 2, 8.0) - 1.0e6) < 1e-6
