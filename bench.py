@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--seconds", type=float, default=5.0, help="serving: length of the arrival trace")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests in flight at once")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
+    ap.add_argument("--policy", default="smallest", choices=["fifo", "smallest"],
+                    help="serving: admission order of the concurrent run (smallest first, 0.25 s maximum wait)")
+    ap.add_argument("--fresh-buffers", action="store_true",
+                    help="serving: new device buffers per request (direct launches) instead of per-instance buffers")
     # batching: many signals of uneven lengths, each with its own plan
     ap.add_argument("--batch", action="store_true", help="measure a batch of uneven-length signals")
     ap.add_argument("--batch-signals", type=int, default=512, help="batch: number of signals")
@@ -366,17 +370,21 @@ def run_serving(args):
         r.signal = pool[r.N]
     budget = int(args.budget_gb * (1 << 30))
     out = {}
-    for label, slots in (("concurrent", args.slots), ("serial", 1)):
+    for label, slots, policy in (("concurrent", args.slots, args.policy), ("concurrent_fifo", args.slots, "fifo"),
+                                 ("serial", 1, "fifo")):
         for r in trace:
             r.t_admit = r.t_done = float("nan")
-        srv = serving.Server(budget, slots=slots, plan_cache_bytes=budget // 2)
+        srv = serving.Server(budget, slots=slots, plan_cache_bytes=budget // 2,
+                             reuse_buffers=not args.fresh_buffers, policy=policy)
         keys = sorted({r.key for r in trace})
         for k in keys:                                       # resident plans
             srv.cache.release(k, srv.cache.acquire(k))
         srv.cache.hits = srv.cache.misses = 0
-        # one untimed pass over the shapes (first-use costs), then the timed trace
-        warm = [serving.Request(i, *k, 0.0, signal=pool[k[0]]) for i, k in enumerate(keys)]
-        serving.run_trace(srv, warm)
+        # two untimed passes over the shapes (first-use costs; the second captures each
+        # instance's graph), then the timed trace
+        for _ in range(2):
+            warm = [serving.Request(i, *k, 0.0, signal=pool[k[0]]) for i, k in enumerate(keys)]
+            serving.run_trace(srv, warm)
         srv.completed.clear()
         torch.cuda.synchronize()
         out[label] = serving.run_trace(srv, [dataclasses_replace(r) for r in trace])
@@ -386,11 +394,14 @@ def run_serving(args):
             "p50_ms": out["concurrent"]["p50_ms"], "p99_ms": out["concurrent"]["p99_ms"],
             "serial_p50_ms": out["serial"]["p50_ms"], "serial_p99_ms": out["serial"]["p99_ms"],
             "offered_scale_samples_per_s": mean_units * len(trace) / args.seconds,
-            "concurrent": out["concurrent"], "serial": out["serial"],
+            "concurrent": out["concurrent"], "concurrent_fifo": out["concurrent_fifo"], "serial": out["serial"],
             "config": {"rate_per_s": args.rate, "seconds": args.seconds, "requests": len(trace),
-                       "slots": args.slots, "budget_gb": args.budget_gb, "N": "2^10..2^24 (powers of two)",
+                       "slots": args.slots, "policy": args.policy, "budget_gb": args.budget_gb,
+                       "N": "2^10..2^24 (powers of two)",
                        "n_scales": "16..128", "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],
-                       "plans": "resident, created before the trace"},
+                       "plans": "resident, created before the trace",
+                       "buffers": "new per request" if args.fresh_buffers
+                       else "per plan instance up to 64 MiB (graph replay), new per request above"},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
 

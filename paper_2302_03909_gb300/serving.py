@@ -3,12 +3,15 @@
 Requests (a signal, its scales, a wavelet and a boundary) arrive over time.
 The loop has three parts:
 
-* ``Admission``: a FIFO queue admitted against a device-memory budget.  A
+* ``Admission``: a queue admitted against a device-memory budget.  A
   request needs its signal, its W and its spectrum, plus the workspace of a
-  plan instance when none is idle.  Requests are admitted in arrival order:
-  the head of the queue waits for memory and for a free slot, and nothing
-  overtakes it.  A request larger than the whole budget is rejected at
-  submission.
+  plan instance when none is idle.  With the "fifo" policy requests are
+  admitted in arrival order: the head of the queue waits for memory and for a
+  free slot, and nothing overtakes it.  With "smallest" the smallest queued
+  request (by scale-samples) goes first, except that a request waiting longer
+  than ``max_wait_s`` goes before any other (oldest first), so large requests
+  are delayed but not starved.  A request larger than the whole budget is
+  rejected at submission.
 * ``PlanCache``: plans resident on the device, keyed by request shape.  A
   plan instance runs on one stream at a time (its workspace is shared), so a
   key can have several instances.  Idle instances are evicted
@@ -16,7 +19,15 @@ The loop has three parts:
 * ``Server``: ``slots`` CUDA streams.  An admitted request takes a free slot
   and a plan instance, copies its signal to the device, runs
   ``cwt_exec_with_power`` and records an event; completions are found by
-  polling the events, and free their memory and slot.
+  polling the events, and free their memory and slot.  By default a plan
+  instance of a small shape (signal + W + spectrum up to ``reuse_max_bytes``)
+  owns its buffers, so its calls repeat the same pointers and the library
+  replays the instance's captured CUDA graph: one graph launch per request
+  instead of a launch sequence, which is what small requests are dominated
+  by.  Larger shapes get new buffers per request: their launch cost is small
+  against their run time, and instances holding their W would crowd the plan
+  cache.  A result the server keeps is copied out of the instance's W on the
+  request's stream.
 
 ``run_trace`` replays a timed arrival trace (open loop) and reports latency
 percentiles; ``poisson_trace`` draws the arrivals.  Both the admission and
@@ -117,10 +128,14 @@ class PlanCache:
 
 
 class Admission:
-    """FIFO admission against a byte budget and a number of slots."""
+    """Admission against a byte budget and a number of slots ("fifo" or
+    "smallest" first with a maximum wait)."""
 
-    def __init__(self, budget_bytes: int, slots: int):
+    def __init__(self, budget_bytes: int, slots: int, policy: str = "fifo", max_wait_s: float = 0.25):
+        if policy not in ("fifo", "smallest"):
+            raise ValueError(policy)
         self.budget, self.slots = budget_bytes, slots
+        self.policy, self.max_wait = policy, max_wait_s
         self.queue: "collections.deque[Request]" = collections.deque()
         self.in_flight_bytes = 0
         self.free_slots = list(range(slots))[::-1]
@@ -131,15 +146,19 @@ class Admission:
                              f"over the {self.budget}-byte budget")
         self.queue.append(req)
 
-    def next_admissible(self, need: Callable[[Request], int]) -> Optional[Tuple[Request, int, int]]:
-        """Pops the queue head if a slot is free and its bytes fit: (request, slot, bytes)."""
+    def next_admissible(self, need: Callable[[Request], int], now: float = 0.0) -> Optional[Tuple[Request, int, int]]:
+        """Pops the next request by the policy if a slot is free and its bytes
+        fit: (request, slot, bytes).  The chosen request waits for memory;
+        nothing else overtakes it meanwhile."""
         if not self.queue or not self.free_slots:
             return None
         req = self.queue[0]
+        if self.policy == "smallest" and now - req.t_arrival <= self.max_wait:
+            req = min(self.queue, key=lambda q: (len(q.scales) * q.N, q.t_arrival))
         b = need(req)
         if self.in_flight_bytes + b > self.budget:
             return None
-        self.queue.popleft()
+        self.queue.remove(req)
         self.in_flight_bytes += b
         return req, self.free_slots.pop(), b
 
@@ -152,33 +171,52 @@ class Server:
     """Runs admitted requests on ``slots`` CUDA streams of one device."""
 
     def __init__(self, budget_bytes: int, slots: int = 4, plan_cache_bytes: Optional[int] = None,
-                 keep_results: bool = False, device: int = 0):
+                 keep_results: bool = False, device: int = 0, reuse_buffers: bool = True,
+                 reuse_max_bytes: int = 64 << 20, policy: str = "fifo", max_wait_s: float = 0.25):
         import torch
 
         import paper_2302_03909_gb300 as cwt
         self.torch, self.cwt = torch, cwt
         self.dev = torch.device("cuda", device)
-        self.adm = Admission(budget_bytes, slots)
+        self.adm = Admission(budget_bytes, slots, policy, max_wait_s)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.reuse = reuse_buffers
+        self.reuse_max = reuse_max_bytes
         self.cache = PlanCache(self._make_plan, plan_cache_bytes if plan_cache_bytes is not None
-                               else budget_bytes // 4)
+                               else budget_bytes // 4, size_of=self._size_of)
         self.keep = keep_results
         self.in_flight: List[tuple] = []      # (req, slot, bytes, plan, event, tensors)
         self.completed: List[Request] = []
         self._ws_guess: Dict[tuple, int] = {}
 
     def _make_plan(self, key):
+        torch = self.torch
         N, scales, wavelet, boundary = key
         p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary)
-        self._ws_guess[key] = p.workspace_bytes
+        p._io, p._io_bytes = None, 0
+        if self._owns_buffers(Request(-1, *key, 0.0)):
+            p._io = (torch.empty(N, dtype=torch.float32, device=self.dev), p.empty_output(self.dev),
+                     torch.empty(p.n_scales, dtype=torch.float64, device=self.dev))
+            p._io_bytes = sum(t.numel() * t.element_size() for t in p._io)
+        self._ws_guess[key] = self._size_of(p)
         return p
 
+    def _owns_buffers(self, req: Request) -> bool:
+        return self.reuse and req.io_bytes <= self.reuse_max
+
+    @staticmethod
+    def _size_of(p) -> int:
+        return p.workspace_bytes + getattr(p, "_io_bytes", 0)
+
     def _need(self, req: Request) -> int:
-        # a new instance's workspace counts against the budget while it is busy;
-        # the size is known once the shape's first plan exists, so the first
-        # request of a never-seen shape is admitted on its own buffers only
+        # a new instance (workspace, and its own buffers) counts against the
+        # budget while it is busy; the size is known once the shape's first plan
+        # exists, so the first request of a never-seen shape is admitted on its
+        # own buffers only.  Requests that run in an instance's buffers need
+        # nothing more, unless their result is kept (a copy).
         extra = 0 if self.cache.has_idle(req.key) else self._ws_guess.get(req.key, 0)
-        return req.io_bytes + extra
+        own = req.io_bytes if (not self._owns_buffers(req) or self.keep) else 0
+        return own + extra
 
     def submit(self, req: Request):
         self.adm.submit(req)
@@ -188,11 +226,16 @@ class Server:
         st = self.streams[slot]
         plan = self.cache.acquire(req.key)
         with torch.cuda.stream(st):
-            sig = torch.empty(req.N, dtype=torch.float32, device=self.dev)
+            if plan._io is not None:
+                sig, W, sp = plan._io
+            else:
+                sig = torch.empty(req.N, dtype=torch.float32, device=self.dev)
+                W = plan.empty_output(self.dev)
+                sp = torch.empty(plan.n_scales, dtype=torch.float64, device=self.dev)
             sig.copy_(req.signal, non_blocking=True)
-            W = plan.empty_output(self.dev)
-            sp = torch.empty(plan.n_scales, dtype=torch.float64, device=self.dev)
             self.cwt.cwt_exec_with_power(plan, sig, W, sp, st)
+            if self.keep and plan._io is not None:
+                W, sp = W.clone(), sp.clone()
             ev = torch.cuda.Event()
             ev.record(st)
         req.t_admit = now
@@ -216,7 +259,7 @@ class Server:
                 still.append(item)
         self.in_flight = still
         while True:
-            nxt = self.adm.next_admissible(self._need)
+            nxt = self.adm.next_admissible(self._need, now)
             if nxt is None:
                 break
             self._launch(*nxt, now)

@@ -88,3 +88,25 @@ def test_poisson_trace_shape():
     assert {r.wavelet for r in tr} == {"gdw", "morlet"} and {r.boundary for r in tr} == {"periodic", "zero"}
     tr2 = serving.poisson_trace(400.0, 2.0, seed=3)
     assert [(r.N, r.key) for r in tr] == [(r.N, r.key) for r in tr2]
+
+
+def test_admission_smallest_first_with_a_maximum_wait():
+    big = req(0, N=1 << 14, S=16, t=0.0)
+    small = [req(i, t=0.01 * i) for i in range(1, 4)]
+    adm = serving.Admission(budget_bytes=1 << 30, slots=1, policy="smallest", max_wait_s=0.5)
+    for x in [big] + small:
+        adm.submit(x)
+    order = []
+    now = 0.1
+    while adm.queue:
+        nxt = adm.next_admissible(lambda q: q.io_bytes, now)
+        order.append(nxt[0].rid)
+        adm.done(nxt[1], nxt[2])
+    assert order == [1, 2, 3, 0]                       # smaller requests overtake the large head
+    # once the head has waited longer than max_wait it goes first
+    adm = serving.Admission(budget_bytes=1 << 30, slots=1, policy="smallest", max_wait_s=0.5)
+    for x in [big] + small:
+        adm.submit(x)
+    assert adm.next_admissible(lambda q: q.io_bytes, 0.6)[0].rid == 0
+    with pytest.raises(ValueError):
+        serving.Admission(1, 1, policy="lifo")
