@@ -1,0 +1,112 @@
+"""The identities behind the GPU path's own ways of evaluating the FFTCWT,
+checked with the oracle alone (every transform below is the oracle's Eqs. 8-10
+at the stated padded length M).
+
+* Zero boundary, short wavelets: the M = 2N transform equals the N-periodic
+  one minus the wrapped terms of the dilated wavelet's response h.
+* Periodic boundary, any N: the N-periodic transform equals the zero-boundary
+  transform of the signal extended periodically by E on each side, padded to
+  M >= N + 3E, on the window [E, E + N).
+* Zero boundary, any N: any padded length M' >= N + E + 1 gives the first N
+  outputs of the M = pow2 >= 2N transform.
+
+Each needs the dilated wavelet to be short (negligible beyond E samples) and
+its spectrum to be negligible at the Nyquist frequency; the last test shows
+an identity failing where the second condition does not hold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+OMEGA0 = 6.0
+CHI = {"gdw": 12.5, "morlet": 8.5}       # |psi(x)| is negligible beyond |x| = CHI
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def pow2_at_least(n):
+    return 1 << int(math.ceil(math.log2(n)))
+
+
+def support(w, s):
+    return int(math.ceil(CHI[w] * s)) + 1
+
+
+def nyquist_clear(orc, w, s):
+    k = np.linspace(0.0, 40.0, 4001)
+    peak = np.max(np.abs(orc.psi_hat(w, k, OMEGA0)))
+    return abs(orc.psi_hat(w, [math.pi * s], OMEGA0)[0]) < 1e-7 * peak
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("w,s", [("gdw", 2.0), ("gdw", 9.0), ("morlet", 4.0), ("morlet", 7.0)])
+def test_zero_boundary_is_periodic_minus_wrapped_terms(orc, w, s):
+    N = 1024
+    E = support(w, s)
+    assert nyquist_clear(orc, w, s) and E < N // 4
+    f = synth.lognormal_field(N, seed=31)
+    W_N = orc.cwt_fft(f, [s], w, M=N, omega0=OMEGA0)[0]
+    W_0 = orc.cwt_fft(f, [s], w, M=2 * N, omega0=OMEGA0)[0]
+    # h(j), |j| <= E: the zero-boundary response to a unit impulse at m0
+    m0 = N // 2
+    imp = np.zeros(N)
+    imp[m0] = 1.0
+    resp = orc.cwt_fft(imp, [s], w, M=2 * N, omega0=OMEGA0)[0]
+    h = {j: resp[m0 + j] for j in range(-E, E + 1)}
+    fix = np.zeros(N, dtype=complex)
+    for n in range(E):                    # left edge: m = N + n - j, j in [n + 1, E]
+        fix[n] = sum(h[j] * f[N + n - j] for j in range(n + 1, E + 1))
+    for n in range(N - E, N):             # right edge: m = n - N - j, j in [-E, n - N]
+        fix[n] = sum(h[j] * f[n - N - j] for j in range(-E, n - N + 1))
+    assert rel(W_N - fix, W_0) < 1e-11
+    assert np.max(np.abs(W_N[E:N - E] - W_0[E:N - E])) < 1e-11 * np.max(np.abs(W_0))
+    assert rel(W_N, W_0) > 1e-6           # the wrapped terms are not negligible on their own
+
+
+@pytest.mark.parametrize("N", [1000, 997, 1500])
+@pytest.mark.parametrize("w,s", [("gdw", 2.0), ("gdw", 30.0), ("morlet", 4.0), ("morlet", 60.0)])
+def test_periodic_any_n_is_zero_boundary_of_the_extended_signal(orc, N, w, s):
+    E = support(w, s)
+    assert nyquist_clear(orc, w, s)
+    f = synth.lognormal_field(N, seed=N)
+    W_N = orc.cwt_fft(f, [s], w, M=N, omega0=OMEGA0)[0]            # the oracle's own N-point FFTCWT
+    g = f[(np.arange(N + 2 * E) - E) % N]
+    Mg = pow2_at_least(N + 3 * E)
+    W_g = orc.cwt_fft(g, [s], w, M=Mg, omega0=OMEGA0)[0][E:E + N]
+    assert rel(W_g, W_N) < 1e-11
+
+
+@pytest.mark.parametrize("N", [1100, 3001])
+@pytest.mark.parametrize("w,s", [("gdw", 2.0), ("gdw", 40.0), ("morlet", 4.0), ("morlet", 50.0)])
+def test_zero_boundary_needs_only_n_plus_e_padding(orc, N, w, s):
+    E = support(w, s)
+    assert nyquist_clear(orc, w, s)
+    f = synth.lognormal_field(N, seed=N + 1)
+    M = pow2_at_least(2 * N)
+    Mp = pow2_at_least(N + E + 1)
+    assert Mp < M
+    W = orc.cwt_fft(f, [s], w, M=M, omega0=OMEGA0)[0]
+    Wp = orc.cwt_fft(f, [s], w, M=Mp, omega0=OMEGA0)[0]
+    assert rel(Wp, W) < 1e-11
+
+
+def test_a_spectrum_cut_at_nyquist_breaks_the_identities(orc):
+    """The Morlet at s = 2 has a large spectrum at the Nyquist frequency; its
+    band-limited wavelet rings, so shorter padding changes the result."""
+    N, s = 1000, 2.0
+    assert not nyquist_clear(orc, "morlet", s)
+    f = synth.lognormal_field(N, seed=5)
+    W = orc.cwt_fft(f, [s], "morlet", M=pow2_at_least(2 * N), omega0=OMEGA0)[0]
+    Wp = orc.cwt_fft(f, [s], "morlet", M=pow2_at_least(N + support("morlet", s) + 1), omega0=OMEGA0)[0]
+    assert rel(Wp, W) > 1e-5
