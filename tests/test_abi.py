@@ -91,3 +91,36 @@ def test_null_plan_pointers_rejected(cwt):
     assert lib.cwt_plan_destroy(None) == 0
     n = ctypes.c_int32()
     assert lib.cwt_scales_paper_grid(1, 0, 6.0, 2, None, ctypes.byref(n)) == 1
+
+
+def test_batch_and_options_entry_points_check_their_arguments(cwt):
+    """Checked on the host before any CUDA call, so this runs without a GPU."""
+    lib = cwt.load_library()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)()
+    assert lib.cwt_batch_create(None, arr, arr, arr, None, 1, 1) == 1
+    assert lib.cwt_batch_create(ctypes.byref(h), None, arr, arr, None, 1, 1) == 1
+    assert lib.cwt_batch_create(ctypes.byref(h), arr, arr, arr, None, 0, 1) == 1          # n < 1
+    assert lib.cwt_batch_create(ctypes.byref(h), arr, arr, arr, None, 1, 1) == 1          # NULL plan
+    assert h.value is None
+    assert lib.cwt_batch_exec(None, None) == 1
+    assert lib.cwt_batch_info(None, None, None, None, None) == 1
+    assert lib.cwt_batch_destroy(None) == 0
+    assert lib.cwt_plan_get_opts(None, None) == 1
+    with pytest.raises(ValueError):
+        cwt.cwt_batch_create([])
+
+
+def test_plan_options_struct_matches_the_header(cwt):
+    """The binding's mirror of cwt_plan_opts has the header's field order and
+    the defaults the library fills in."""
+    o = cwt._Opts()
+    cwt.load_library().cwt_plan_opts_default(ctypes.byref(o))
+    assert ctypes.sizeof(o) == 56
+    assert (o.omega0, o.dx, o.scale_unit, o.input_dtype, o.fft_len) == (6.0, 1.0, 0, 0, 0)
+    assert (o.eps_trunc, o.min_ctas, o.tune, o.wide_batch_bytes) == (1e-10, 0, 0, 0)
+    with open(os.path.join(ROOT, "include", "cwt.h")) as fh:
+        text = fh.read()
+    body = text[text.index("typedef struct {", text.index("cwt_input_dtype;")):text.index("} cwt_plan_opts;")]
+    fields = re.findall(r"^\s+(?:double|int32_t|int64_t)\s+(\w+);", body, flags=re.M)
+    assert fields == [name for name, _ in cwt._Opts._fields_]
