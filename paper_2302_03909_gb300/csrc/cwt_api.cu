@@ -1,5 +1,6 @@
-// Host side of the GB300 FFTCWT: planner, workspace, launches and the C ABI
-// declared in include/cwt.h.  Transform definition: Wang & He (RASTI 2023,
+// Host side of the GB300 FFTCWT: planner, workspace, launches, plan-time
+// tuning, batches of grouped launches and the C ABI declared in
+// include/cwt.h.  Transform definition: Wang & He (RASTI 2023,
 // arXiv:2302.03909), Sec. 3.1, Eqs. 8-10; power spectrum Eq. 42.
 #include <cuda_runtime.h>
 

@@ -23,6 +23,12 @@
 //
 // Real wavelets (GDW): two scales share one complex transform,
 // Z = Z_a + i Z_b with Z_a, Z_b Hermitian, so Re X = W_a and Im X = W_b.
+//
+// Every kernel is a body taking its argument and its block coordinates (Cta),
+// with two entry points: the plain kernel (one launch of one plan) and the
+// grouped kernel "_g" (the launches of one kernel made by many plans, merged
+// into one grid; see GroupMap).  Both run the same body, so they compute the
+// same values bit for bit.
 #pragma once
 
 #include <cuda_runtime.h>
