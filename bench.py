@@ -331,6 +331,29 @@ def fft_library_baseline(f, sc, wavelet, plans, outs, flush, stream, steps, warm
     return out
 
 
+def batch_cpu_baseline(reqs, budget_s: float):
+    """The FP64 oracle (FFT tier, all host cores) over the batch's first
+    signals, one after another, until about budget_s has passed: a bounded
+    sample of the batch, reported per scale-sample."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    units, n = 0, 0
+    t0 = time.perf_counter()
+    for r in reqs:
+        f = np.asarray(r.signal, dtype=np.float32).astype(np.float64)
+        M = r.N if r.boundary == "periodic" else 1 << int(math.ceil(math.log2(2 * r.N)))
+        oracle.cwt_fft(f, np.asarray(r.scales), r.wavelet, M=M, nthreads=cores)
+        units += len(r.scales) * r.N
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": units / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {n} of {len(reqs)} signals ({units} scale-samples), FP64 FFT tier, "
+                      f"OpenMP over scales; {t:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -489,9 +512,10 @@ def run_batch(args):
     del graph
     for p in plans:
         p.close()
+    cpu = None if args.no_cpu_baseline else batch_cpu_baseline(reqs, args.cpu_seconds)
     line = {"impl": "ours", "metric": "CWT scale-samples/s, batch of uneven lengths", "unit": "scale-samples/s",
             "higher_is_better": True, "value": units / out["grouped_s"], "graph": units / out["graph_s"],
-            "one_by_one": units / out["one_by_one_s"],
+            "one_by_one": units / out["one_by_one_s"], "cpu_baseline": cpu,
             "detail": out,
             "config": {"signals": len(reqs), "N": "log-uniform integers in [1024, 65536]", "n_scales": "16..96",
                        "scale_samples": units, "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],

@@ -21,3 +21,18 @@ def test_traffic_scales_with_the_launch_size():
 def test_weak_scaling_value_counts_all_ranks():
     # 4 steps of 1000 units on each of 2 ranks in 8 ms (max over ranks)
     assert abs(bench.weak_scaling_value(1000.0, 4, 2, 8.0) - 1.0e6) < 1e-6
+
+
+def test_batch_cpu_baseline_times_a_bounded_sample():
+    import numpy as np
+    from paper_2302_03909_gb300 import serving
+    reqs = []
+    for i, (N, wav, bnd) in enumerate([(300, "gdw", "periodic"), (257, "morlet", "zero"), (512, "gdw", "zero")]):
+        r = serving.Request(i, N, tuple(np.geomspace(2.0, N / 4, 5)), wav, bnd, 0.0)
+        r.signal = np.random.default_rng(i).standard_normal(N).astype(np.float32)
+        reqs.append(r)
+    cb = bench.batch_cpu_baseline(reqs, 0.0)          # stops after the first signal
+    assert cb["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] >= 1
+    assert cb["sample"].startswith("the first 1 of 3 signals (1500 scale-samples)")
+    cb = bench.batch_cpu_baseline(reqs, 60.0)
+    assert cb["sample"].startswith("the first 3 of 3 signals")
