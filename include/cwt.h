@@ -200,9 +200,13 @@ typedef enum {
     CWT_KCLASS_COUNT = 5
 } cwt_kernel_class;
 
-/* Timing hook.  enable != 0 makes the following device calls of this plan
- * record a CUDA event pair around every kernel launch on the call's stream;
- * any call resets the totals.  Costs one event record per launch boundary. */
+/* Timing hook.  enable = 1 makes the following device calls of this plan
+ * record a CUDA event pair around every kernel launch, on the stream the
+ * launch is made on (launches of independent work still overlap on the side
+ * streams); enable = 2 also puts every launch on the call's stream, one after
+ * another, so that each event pair times one kernel running alone; 0 turns
+ * the hook off.  Any call resets the totals.  Costs one event record per
+ * launch boundary.  Other values: CWT_ERR_INVALID_ARG. */
 cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable);
 
 /* Totals since cwt_plan_set_timing for one cwt_kernel_class: summed launch

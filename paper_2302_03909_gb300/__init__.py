@@ -362,9 +362,14 @@ def cwt_wavelet_power_noalloc(W, spectrum, stream=None):
     return spectrum
 
 
-def cwt_plan_set_timing(plan: Plan, enable: bool = True):
-    """Record a CUDA event pair around each kernel launch of the following calls."""
-    _check(load_library().cwt_plan_set_timing(plan._h, int(bool(enable))), plan)
+def cwt_plan_set_timing(plan: Plan, enable=True):
+    """Record a CUDA event pair around each kernel launch of the following calls.
+
+    enable: False/0 off; True/1 events on each launch's own stream; 2 or
+    "serial" also runs every launch on the call's stream, one after another, so
+    that each event pair times one kernel alone."""
+    mode = 2 if enable == "serial" else int(enable)
+    _check(load_library().cwt_plan_set_timing(plan._h, mode), plan)
 
 
 def cwt_plan_get_timing(plan: Plan) -> dict:

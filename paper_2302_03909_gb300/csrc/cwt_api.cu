@@ -929,8 +929,11 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if ((st = run_launches(p->child, signal, Wc, sc, s)) != CWT_OK) return st;
         return edge_fix(s);
     }
+    // timing mode 2 serialises every launch on the call's stream, so that each
+    // launch's event pair measures that kernel alone
+    const bool serial = p->timing == 2;
     cudaStream_t fs = s;                         // stream of this plan's forward transform
-    if (p->child) {
+    if (p->child && !serial) {
         if ((st = ev_record(p, p->ev_pre, s)) != CWT_OK) return st;
         if ((st = ev_wait(p, p->side[0], p->ev_pre)) != CWT_OK) return st;
         fs = p->side[0];
@@ -998,7 +1001,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     //      streams forked after the forward transform; each stream has its own
     //      intermediate Y.
     const int nwork = (int)(p->groups.size() + p->wide.size());
-    const int nstreams = std::min(nwork, cwt_plan::kSide + 1);
+    const int nstreams = serial ? 1 : std::min(nwork, cwt_plan::kSide + 1);
     cudaStream_t streams[cwt_plan::kSide + 1] = {s};
     if (nstreams > 1) {
         if ((st = ev_record(p, p->ev_fork, s)) != CWT_OK) return st;
@@ -1649,7 +1652,8 @@ cwt_status cwt_plan_set_timing(cwt_plan* plan, int32_t enable) {
     if (!plan) return CWT_ERR_INVALID_ARG;
     if (!plan->pending.empty()) cudaDeviceSynchronize();
     release_events(plan);
-    plan->timing = enable != 0;
+    if (enable < 0 || enable > 2) return CWT_ERR_INVALID_ARG;
+    plan->timing = enable;
     if (plan->child) cwt_plan_set_timing(plan->child, enable);
     for (cwt_plan* q : plan->subs) cwt_plan_set_timing(q, enable);
     for (int c = 0; c < CWT_KCLASS_COUNT; c++) {

@@ -113,7 +113,7 @@ struct cwt_plan {
 
     // timing hook (cwt_plan_set_timing)
     struct TimedLaunch { int cls; cudaEvent_t a, b; double bytes; };
-    bool timing = false;
+    int timing = 0;                       // 1: events per launch; 2: also every launch on the call's stream
     std::vector<cudaEvent_t> ev_pool;
     std::vector<TimedLaunch> pending;
     double t_ms[CWT_KCLASS_COUNT] = {};

@@ -3,9 +3,12 @@
 Requests (a signal, its scales, a wavelet and a boundary) arrive over time.
 The loop has three parts:
 
-* ``Admission``: a queue admitted against a device-memory budget.  A
-  request needs its signal, its W and its spectrum, plus the workspace of a
-  plan instance when none is idle.  With the "fifo" policy requests are
+* ``Admission``: a queue admitted against a device-memory budget
+  (``Ledger``).  A request needs its signal, its W and its spectrum, plus the
+  workspace of its plan instance; idle cached instances count against the
+  same budget and are evicted to make room.  An instance of a never-seen
+  shape is charged an upper bound of its workspace (``workspace_bound``)
+  until it exists.  With the "fifo" policy requests are
   admitted in arrival order: the head of the queue waits for memory and for a
   free slot, and nothing overtakes it.  With "smallest" the smallest queued
   request (by scale-samples) goes first, except that a request waiting longer
@@ -82,7 +85,8 @@ class PlanCache:
         self.factory, self.max_bytes, self.size_of, self.close = factory, max_bytes, size_of, close
         self.idle: "collections.OrderedDict[tuple, List]" = collections.OrderedDict()
         self.busy = 0
-        self.bytes = 0
+        self.bytes = 0          # all live instances, busy or idle
+        self.idle_bytes = 0     # idle instances only
         self.hits = self.misses = self.evictions = 0
 
     def has_idle(self, key) -> bool:
@@ -95,6 +99,7 @@ class PlanCache:
             p = lst.pop()
             if not lst:
                 del self.idle[key]
+            self.idle_bytes -= self.size_of(p)
         else:
             self.misses += 1
             p = self.factory(key)
@@ -107,24 +112,47 @@ class PlanCache:
         self.busy -= 1
         self.idle.setdefault(key, []).append(p)
         self.idle.move_to_end(key)
+        self.idle_bytes += self.size_of(p)
         self.trim()
 
-    def trim(self):
-        while self.bytes > self.max_bytes and self.idle:
-            key, lst = next(iter(self.idle.items()))
+    def _evict_one(self, avoid=None) -> bool:
+        for key, lst in self.idle.items():
+            if avoid is not None and key == avoid:
+                continue
             p = lst.pop(0)
             if not lst:
                 del self.idle[key]
-            self.bytes -= self.size_of(p)
+            n = self.size_of(p)
+            self.bytes -= n
+            self.idle_bytes -= n
             self.close(p)
             self.evictions += 1
+            return True
+        return False
+
+    def trim(self):
+        while self.bytes > self.max_bytes and self.idle:
+            self._evict_one()
+
+    def evict_idle(self, nbytes: int, avoid=None) -> int:
+        """Evicts idle instances, least recently used first and never of the
+        key ``avoid``, until ``nbytes`` are freed or none is left to evict;
+        returns the bytes freed."""
+        freed = 0
+        while freed < nbytes:
+            before = self.idle_bytes
+            if not self._evict_one(avoid):
+                break
+            freed += before - self.idle_bytes
+        return freed
 
     def clear(self):
         for lst in self.idle.values():
             for p in lst:
                 self.close(p)
+                self.bytes -= self.size_of(p)
         self.idle.clear()
-        self.bytes = 0
+        self.idle_bytes = 0
 
 
 class Admission:
@@ -146,17 +174,20 @@ class Admission:
                              f"over the {self.budget}-byte budget")
         self.queue.append(req)
 
-    def next_admissible(self, need: Callable[[Request], int], now: float = 0.0) -> Optional[Tuple[Request, int, int]]:
+    def next_admissible(self, need: Callable[[Request], int], now: float = 0.0,
+                        room: Optional[Callable[[Request, int], bool]] = None) -> Optional[Tuple[Request, int, int]]:
         """Pops the next request by the policy if a slot is free and its bytes
-        fit: (request, slot, bytes).  The chosen request waits for memory;
-        nothing else overtakes it meanwhile."""
+        fit: (request, slot, bytes).  ``room(req, b)`` decides whether b more
+        bytes fit (it may free memory to make them fit); by default they fit
+        while the bytes in flight stay within the budget.  The chosen request
+        waits for memory; nothing else overtakes it meanwhile."""
         if not self.queue or not self.free_slots:
             return None
         req = self.queue[0]
         if self.policy == "smallest" and now - req.t_arrival <= self.max_wait:
             req = min(self.queue, key=lambda q: (len(q.scales) * q.N, q.t_arrival))
         b = need(req)
-        if self.in_flight_bytes + b > self.budget:
+        if not (room(req, b) if room is not None else self.in_flight_bytes + b <= self.budget):
             return None
         self.queue.remove(req)
         self.in_flight_bytes += b
@@ -165,6 +196,102 @@ class Admission:
     def done(self, slot: int, nbytes: int):
         self.in_flight_bytes -= nbytes
         self.free_slots.append(slot)
+
+
+def _pow2(x: int) -> int:
+    return 1 << max(0, int(x - 1).bit_length())
+
+
+def _plan_bound(M: int, S: int) -> int:
+    """Upper bound on the device workspace of one plan of transform length M
+    with S rows: the spectrum (M/2 + 1 complex64) and its transposed copy (M),
+    the wide-scale intermediate (three streams, each max(M, 4 Mi) complex64),
+    the band values (at most 4096 complex64 per row), the power partial sums
+    (fewer than M / 256 per row), the edge tables of a zero-boundary plan
+    (2 x 4096 + 1 complex64 per row) and 2 MiB of small tables."""
+    return 16 * M + 3 * max(8 * M, 32 << 20) + S * (96 << 10) + S * (M // 32) + (2 << 20)
+
+
+def workspace_bound(N: int, scales, wavelet: str, boundary: str) -> int:
+    """Upper bound on the device workspace of the library's plan for one
+    request shape, from the same structure the planner uses: the zero
+    boundary pads to M = pow2 >= 2N, with a periodic N-point child plan when N
+    is a power of two and shorter sub-plans (M/2 and M) otherwise; the
+    periodic boundary uses M = N for a power of two, else sub-plans of length
+    pow2 >= N + 3E per row (E = ceil(chi s) + 1 the dilated wavelet's support,
+    chi = 12.5 for the GDW and 8.5 for the Morlet) over a buffer of
+    N + 2 max E samples."""
+    S = len(scales)
+    if boundary == "zero":
+        M = _pow2(2 * N)
+        return _plan_bound(M, S) + (_plan_bound(N, S) if N == _pow2(N) else _plan_bound(M // 2, S))
+    if N == _pow2(N):
+        return _plan_bound(N, S)
+    chi = 12.5 if wavelet == "gdw" else 8.5
+    E = [int(math.ceil(chi * float(sv))) + 1 for sv in scales]
+    Ms = sorted({_pow2(N + 3 * e) for e in E})
+    return sum(_plan_bound(M, S) for M in Ms) + 8 * (N + 2 * max(E))
+
+
+class Ledger:
+    """Device memory of a server, kept within one budget: the requests in
+    flight (their own buffers, unless they run in their plan instance's, and
+    their plan instance) plus the idle plan instances of the cache.  A request
+    is admitted when the bytes it adds fit, after evicting idle instances of
+    other shapes if needed; an instance of a never-seen shape is charged
+    ``bound(request)`` until it exists and its size is known."""
+
+    def __init__(self, budget_bytes: int, slots: int, cache: "PlanCache", own_bytes: Callable[[Request], int],
+                 policy: str = "fifo", max_wait_s: float = 0.25,
+                 bound: Callable[[Request], int] = lambda r: workspace_bound(r.N, r.scales, r.wavelet, r.boundary)):
+        self.adm = Admission(budget_bytes, slots, policy, max_wait_s)
+        self.cache, self.own_bytes, self.bound = cache, own_bytes, bound
+        self.known: Dict[tuple, int] = {}      # workspace of an instance, by key
+        self.peak_bytes = 0
+
+    @property
+    def device_bytes(self) -> int:
+        return self.adm.in_flight_bytes + self.cache.idle_bytes
+
+    def submit(self, req: Request):
+        # a request whose own bytes plus a new instance exceed the budget could never run
+        self.adm.submit(req, extra_bytes=self.own_bytes(req) - req.io_bytes
+                        + self.known.get(req.key, self.bound(req)))
+
+    def need(self, req: Request) -> int:
+        """Bytes admitting req adds to the device: its own buffers, and a new
+        instance unless an idle one (already counted) is there."""
+        own = self.own_bytes(req)
+        if self.cache.has_idle(req.key):
+            return own
+        return own + self.known.get(req.key, self.bound(req))
+
+    def room(self, req: Request, b: int) -> bool:
+        over = self.device_bytes + b - self.adm.budget
+        if over > 0:
+            self.cache.evict_idle(over, avoid=req.key)
+        return self.device_bytes + b <= self.adm.budget
+
+    def admit(self, now: float = 0.0):
+        """(request, slot, plan instance, bytes reserved) of the next admitted
+        request, or None."""
+        nxt = self.adm.next_admissible(self.need, now, self.room)
+        if nxt is None:
+            return None
+        req, slot, b = nxt
+        inst = self.cache.acquire(req.key)
+        size = self.cache.size_of(inst)
+        self.known[req.key] = size
+        reserved = self.own_bytes(req) + size
+        # the instance is now in flight: an idle one's bytes move out of the
+        # cache's count, a new one's size replaces the bound it was charged
+        self.adm.in_flight_bytes += reserved - b
+        self.peak_bytes = max(self.peak_bytes, self.device_bytes)
+        return req, slot, inst, reserved
+
+    def finish(self, req: Request, slot: int, inst, reserved: int):
+        self.cache.release(req.key, inst)
+        self.adm.done(slot, reserved)
 
 
 class Server:
@@ -178,16 +305,16 @@ class Server:
         import paper_2302_03909_gb300 as cwt
         self.torch, self.cwt = torch, cwt
         self.dev = torch.device("cuda", device)
-        self.adm = Admission(budget_bytes, slots, policy, max_wait_s)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
         self.reuse = reuse_buffers
         self.reuse_max = reuse_max_bytes
+        self.keep = keep_results
         self.cache = PlanCache(self._make_plan, plan_cache_bytes if plan_cache_bytes is not None
                                else budget_bytes // 4, size_of=self._size_of)
-        self.keep = keep_results
+        self.ledger = Ledger(budget_bytes, slots, self.cache, self._own_bytes, policy, max_wait_s)
+        self.adm = self.ledger.adm
         self.in_flight: List[tuple] = []      # (req, slot, bytes, plan, event, tensors)
         self.completed: List[Request] = []
-        self._ws_guess: Dict[tuple, int] = {}
 
     def _make_plan(self, key):
         torch = self.torch
@@ -198,7 +325,6 @@ class Server:
             p._io = (torch.empty(N, dtype=torch.float32, device=self.dev), p.empty_output(self.dev),
                      torch.empty(p.n_scales, dtype=torch.float64, device=self.dev))
             p._io_bytes = sum(t.numel() * t.element_size() for t in p._io)
-        self._ws_guess[key] = self._size_of(p)
         return p
 
     def _owns_buffers(self, req: Request) -> bool:
@@ -208,23 +334,18 @@ class Server:
     def _size_of(p) -> int:
         return p.workspace_bytes + getattr(p, "_io_bytes", 0)
 
-    def _need(self, req: Request) -> int:
-        # a new instance (workspace, and its own buffers) counts against the
-        # budget while it is busy; the size is known once the shape's first plan
-        # exists, so the first request of a never-seen shape is admitted on its
-        # own buffers only.  Requests that run in an instance's buffers need
-        # nothing more, unless their result is kept (a copy).
-        extra = 0 if self.cache.has_idle(req.key) else self._ws_guess.get(req.key, 0)
-        own = req.io_bytes if (not self._owns_buffers(req) or self.keep) else 0
-        return own + extra
+    def _own_bytes(self, req: Request) -> int:
+        # requests that run in their instance's buffers need nothing of their
+        # own, unless their result is kept (a copy); the instance (workspace
+        # and buffers) is charged by the ledger
+        return req.io_bytes if (not self._owns_buffers(req) or self.keep) else 0
 
     def submit(self, req: Request):
-        self.adm.submit(req)
+        self.ledger.submit(req)
 
-    def _launch(self, req: Request, slot: int, nbytes: int, now: float):
+    def _launch(self, req: Request, slot: int, plan, nbytes: int, now: float):
         torch = self.torch
         st = self.streams[slot]
-        plan = self.cache.acquire(req.key)
         with torch.cuda.stream(st):
             if plan._io is not None:
                 sig, W, sp = plan._io
@@ -251,15 +372,14 @@ class Server:
                 req.t_done = now
                 if self.keep:
                     req.W, req.spectrum = W, sp
-                self.cache.release(req.key, plan)
-                self.adm.done(slot, nbytes)
+                self.ledger.finish(req, slot, plan, nbytes)
                 self.completed.append(req)
                 n += 1
             else:
                 still.append(item)
         self.in_flight = still
         while True:
-            nxt = self.adm.next_admissible(self._need, now)
+            nxt = self.ledger.admit(now)
             if nxt is None:
                 break
             self._launch(*nxt, now)

@@ -36,3 +36,18 @@ def test_batch_cpu_baseline_times_a_bounded_sample():
     assert cb["sample"].startswith("the first 1 of 3 signals (1500 scale-samples)")
     cb = bench.batch_cpu_baseline(reqs, 60.0)
     assert cb["sample"].startswith("the first 3 of 3 signals")
+
+
+def test_default_workload_runs_both_wavelets_and_boundaries_at_n4m_s128():
+    """The default step is the N = 2^22, 128-scale field under the GDW and the
+    Morlet, each with the periodic and the zero boundary."""
+    import synth
+    parts = bench.workload_parts(bench.DEFAULT_WORKLOAD)
+    assert sorted(synth.WORKLOADS[q]["wavelet"] for q in parts) == ["gdw", "morlet"]
+    for q in parts:
+        w = synth.WORKLOADS[q]
+        assert w["n"] == 1 << 22 and w["n_scales"] == 128
+        assert tuple(w["boundaries"]) == ("periodic", "zero")
+    sigs = [synth.workload_signal(q) for q in parts]
+    assert all((s == sigs[0]).all() for s in sigs)       # one field, transformed four ways
+    assert bench.workload_parts("lognormal_n1m_morlet_s64") == ("lognormal_n1m_morlet_s64",)

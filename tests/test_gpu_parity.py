@@ -219,6 +219,53 @@ def test_lognormal_4m_128_sampled(env, name, boundary):
     _full_case(env, name, boundary, points=192)
 
 
+@pytest.mark.parametrize("name", ["lognormal_n4m_gdw_s128", "lognormal_n4m_morlet_s128"])
+@pytest.mark.parametrize("boundary", ["periodic", "zero"])
+def test_lognormal_4m_128_full(env, name, boundary):
+    """N = 2^22, 128 scales, in the launch configuration the benchmark times
+    (plans tuned at creation, graph replay on a side stream): every output of
+    the whole array against the oracle's FFT tier at the same M, taken 16 rows
+    at a time to bound host memory, and the power spectrum against Eq. 42 of
+    the oracle's rows."""
+    torch, cwt, orc = env
+    f = synth.workload_signal(name)
+    sc = synth.workload_scales(name)
+    wav = synth.WORKLOADS[name]["wavelet"]
+    N = len(f)
+    plan = cwt.cwt_plan_create(N, sc, wav, boundary, tune=True)
+    M_ref = N if boundary == "periodic" else 2 * N
+    assert plan.M == M_ref
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    W = plan.empty_output("cuda")
+    spec = torch.empty(len(sc), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(st):
+        for _ in range(3):                       # direct, capture, replay: the bench's steady state
+            cwt.cwt_exec_with_power(plan, sig, W, spec, st)
+    torch.cuda.synchronize()
+    spec = spec.cpu().numpy()
+    fd = f32(f)
+    row_err = np.empty(len(sc))
+    row_ref = np.empty(len(sc))
+    P = np.empty(len(sc))
+    for r0 in range(0, len(sc), 16):
+        r1 = min(len(sc), r0 + 16)
+        ref = orc.cwt_fft(fd, sc[r0:r1], wav, M=M_ref)
+        got = W[r0:r1].cpu().numpy().astype(np.complex128)
+        row_err[r0:r1] = np.linalg.norm(got - ref, axis=1)
+        row_ref[r0:r1] = np.linalg.norm(ref, axis=1)
+        P[r0:r1] = orc.wavelet_power(ref)
+        del ref, got
+    plan.close()
+    err = float(np.sqrt((row_err ** 2).sum() / (row_ref ** 2).sum()))
+    big = row_ref > 1e-6 * np.sqrt((row_ref ** 2).sum())
+    worst_row = float(np.max(row_err[big] / row_ref[big]))
+    print(f"{name}/{boundary}: rel-L2 {err:.3e}, worst row {worst_row:.3e}")
+    assert err <= TOL
+    assert worst_row <= 10 * TOL
+    assert np.max(np.abs(spec - P) / P) < 1e-4
+
+
 def test_graph_replay_matches_direct_launches(env):
     """On a non-default stream the library captures each plan's launches once and
     replays the graph while the pointers repeat; results equal direct launches."""

@@ -68,3 +68,27 @@ def test_batch_graph_equals_direct_calls():
     del g
     for p, *_ in items:
         p.close()
+
+
+@pytest.mark.parametrize("N,wavelet,boundary,smin,smax,S", [
+    (1 << 10, "gdw", "periodic", 2.0, 256.0, 16),
+    (1 << 16, "morlet", "zero", 4.0, 1 << 14, 64),
+    (5000, "gdw", "periodic", 2.0, 1250.0, 40),
+    (70001, "morlet", "periodic", 4.0, 17500.0, 96),
+    (70001, "gdw", "zero", 2.0, 17500.0, 96),
+    (1 << 22, "morlet", "zero", 4.0, 1 << 20, 128),
+    (1 << 24, "gdw", "periodic", 2.0, 1 << 22, 16),
+])
+def test_workspace_bound_covers_the_plans(N, wavelet, boundary, smin, smax, S):
+    """The admission charges a never-seen shape serving.workspace_bound until
+    its plan exists: the bound must cover the plan's real workspace."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_03909_gb300 as cwt
+    from paper_2302_03909_gb300 import serving
+    sc = tuple(float(x) for x in np.geomspace(smin, smax, S))
+    p = cwt.cwt_plan_create(N, np.asarray(sc), wavelet, boundary)
+    ws = p.workspace_bytes
+    p.close()
+    assert 0 < ws <= serving.workspace_bound(N, sc, wavelet, boundary)

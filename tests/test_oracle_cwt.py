@@ -297,3 +297,28 @@ def test_inverse_cwt_irregular_grid_and_dx(orc):
     # dilations (w~ = 1 / s) give the same numbers as the equivalent w~ grid
     rec2 = orc.icwt(W, 1.0 / wt, "gdw", dx=0.5)
     assert np.allclose(rec2, rec, rtol=0, atol=1e-13 * np.abs(rec).max())
+
+
+def test_env_power_labels_and_fractions(orc):
+    """Eq. 41 on a W built by hand, so that the answer is known without the
+    oracle: |W|^2 = (s+1)^2 on the positions with delta > 0 (the overdense
+    environment), 1e-4 on those with delta < 0, and delta = 0 at a few
+    positions that belong to neither environment.  Swapping the environments,
+    or counting the delta = 0 positions in either, fails this; Eq. 43 alone
+    does not see a swap."""
+    N, S = 1000, 4
+    rng = np.random.default_rng(3)
+    delta = np.where(rng.random(N) < 0.3, 1.5, -0.4)
+    delta[[5, 500, 999]] = 0.0
+    pos, neg = delta > 0, delta < 0
+    phase = np.exp(1j * rng.uniform(0, 2 * np.pi, (S, N)))
+    amp = np.where(pos[None, :], np.arange(1, S + 1)[:, None], 0.01)
+    W = amp * phase
+    pp, pn, fp, fn = orc.env_power(W, delta)
+    assert fp == pos.sum() / N and fn == neg.sum() / N
+    assert fp + fn == pytest.approx(1.0 - 3.0 / N)
+    assert np.allclose(pp, np.arange(1, S + 1) ** 2.0, rtol=1e-13)
+    assert np.allclose(pn, 1e-4, rtol=1e-12)
+    # an environment with no position gets 0 (Eq. 41 over an empty set)
+    pp0, pn0, fp0, fn0 = orc.env_power(W, -np.abs(delta) - 1.0)
+    assert np.all(pp0 == 0.0) and fp0 == 0.0 and fn0 == 1.0

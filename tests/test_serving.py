@@ -110,3 +110,65 @@ def test_admission_smallest_first_with_a_maximum_wait():
     assert adm.next_admissible(lambda q: q.io_bytes, 0.6)[0].rid == 0
     with pytest.raises(ValueError):
         serving.Admission(1, 1, policy="lifo")
+
+
+def test_ledger_keeps_device_bytes_within_the_budget_under_a_burst_of_new_shapes():
+    """Every request of a burst has a shape never seen before, so each needs a
+    new plan instance whose size is unknown until it exists.  The ledger
+    charges the bound for it, counts idle cached instances against the same
+    budget and evicts them to make room: the bytes actually live on the
+    device (instances alive + the buffers of requests in flight) never exceed
+    the budget, and neither does the ledger's own count."""
+    rng = np.random.default_rng(5)
+    alive = {}
+
+    def factory(key):
+        p = FakePlan(key, int(key[0]) * 37 + 1000)      # the real size, known only once made
+        alive[id(p)] = p
+        return p
+
+    def close(p):
+        p.close()
+        alive.pop(id(p))
+
+    cache = serving.PlanCache(factory, max_bytes=10 ** 9, close=close)   # no cap of its own
+    budget = 400_000
+    led = serving.Ledger(budget, slots=3, cache=cache, own_bytes=lambda r: r.io_bytes,
+                         bound=lambda r: int(r.N) * 37 + 5000)         # above every real size
+    reqs = []
+    for i in range(60):
+        N = int(rng.integers(256, 2048))
+        reqs.append(req(i, N=N, S=int(rng.integers(2, 6)), t=0.0))
+        if i % 3 == 0:                                   # some shapes repeat
+            reqs.append(req(1000 + i, N=N, S=len(reqs[-1].scales), t=0.0))
+    for r in reqs:
+        led.submit(r)
+    in_flight, done = [], 0
+
+    def live_bytes():
+        return sum(p.workspace_bytes for p in alive.values()) + sum(x[0].io_bytes for x in in_flight)
+
+    while done < len(reqs):
+        while True:
+            nxt = led.admit()
+            if nxt is None:
+                break
+            in_flight.append(nxt)
+            assert led.device_bytes <= budget
+            assert live_bytes() <= budget
+        assert in_flight, "nothing admitted with an empty device"
+        x = in_flight.pop(int(rng.integers(len(in_flight))))
+        led.finish(*x)
+        done += 1
+        assert led.device_bytes <= budget and live_bytes() <= budget
+    assert led.adm.in_flight_bytes == 0
+    assert led.device_bytes == cache.idle_bytes == sum(p.workspace_bytes for p in alive.values())
+    assert cache.evictions > 0 and led.peak_bytes <= budget
+
+
+def test_workspace_bound_grows_with_the_transform():
+    b = serving.workspace_bound
+    sc = tuple(np.geomspace(4.0, 256.0, 16))
+    assert b(1 << 12, sc, "morlet", "zero") > b(1 << 12, sc, "morlet", "periodic")
+    assert b(5000, sc, "gdw", "periodic") > b(4096, sc, "gdw", "periodic")
+    assert b(1 << 20, sc * 2, "gdw", "zero") > b(1 << 20, sc, "gdw", "zero")
