@@ -64,6 +64,9 @@ def parse_args():
                     help="skip the comparison with the library FFT (torch.fft / cuFFT) written the usual way")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--precisions", default="fp16x3,bf16x3,fp16,bf16",
+                    help="tensor-core forms of the 1024-point DFT stages timed beside FP32 (comma list; "
+                         "empty: none)")
     # narrower cases of a workload for profiler captures (not a bench line)
     ap.add_argument("--boundary", default="both", choices=["both", "periodic", "zero"],
                     help="run one boundary of the workload only")
@@ -578,37 +581,41 @@ def run_ours(args):
     f = rank_signal(parts[0], rank, world)
     N = len(f)
     sig = torch.tensor(f, dtype=torch.float32, device=dev)
-    # every transform of the step: (part, wavelet, boundary, scales, plan, W, spectrum)
-    runs = []
-    subset = None
+    def make_runs(precision="fp32"):
+        """Every transform of the step: (part, wavelet, boundary, scales, plan, W, spectrum)."""
+        out, sub = [], None
+        for part in parts:
+            w = synth.WORKLOADS[part]
+            bounds, sc, sub = workload_subset(args, part)
+            for b in bounds:
+                p = cwt.cwt_plan_create(N, sc, w["wavelet"], b, tune=not args.no_tune, precision=precision)
+                out.append((part, w["wavelet"], b, sc, p, p.empty_output(dev),
+                            torch.empty(len(sc), dtype=torch.float64, device=dev)))
+        return out, sub
+
     t_plan0 = time.perf_counter()
-    for part in parts:
-        w = synth.WORKLOADS[part]
-        bounds, sc, subset = workload_subset(args, part)
-        for b in bounds:
-            p = cwt.cwt_plan_create(N, sc, w["wavelet"], b, tune=not args.no_tune)
-            runs.append((part, w["wavelet"], b, sc, p, p.empty_output(dev),
-                         torch.empty(len(sc), dtype=torch.float64, device=dev)))
+    runs, subset = make_runs()
     t_plan = time.perf_counter() - t_plan0
     plans = [r[4] for r in runs]
     shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes")} for p in plans]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        for _, _, _, _, p, W, sp in runs:
+    def step(rs=None):
+        for _, _, _, _, p, W, sp in (rs or runs):
             cwt.cwt_exec_with_power(p, sig, W, sp, stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    def timed(K: int, timing):
+    def timed(K: int, timing, rs=None):
         """K steps bracketed by a barrier and a synchronize; each step timed with
         CUDA events on the step's stream.  timing: the plans' timing hook (0: the
         library's own path, graph replay; "serial": an event pair around every
         launch, all launches on the step's stream one after another)."""
-        for p in plans:
-            cwt.cwt_plan_set_timing(p, timing)
+        rs = rs or runs
+        for r in rs:
+            cwt.cwt_plan_set_timing(r[4], timing)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         if world > 1:
             torch.distributed.barrier()
@@ -618,7 +625,7 @@ def run_ours(args):
         for k in range(K):
             flush.zero_()
             evs[k][0].record(stream)
-            step()
+            step(rs)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -681,6 +688,34 @@ def run_ours(args):
                "ms_per_step": te * 1e3 / e2e_steps}
         del Wh, sh
 
+    # the tensor-core forms of the 1024-point DFT stages, timed the same way on the same
+    # signal, with their W against this FP32 run's W (the oracle gates are the tests')
+    prec = {}
+    forms = [x for x in args.precisions.split(",") if x] if rank == 0 and world == 1 else []
+    for form in forms:
+        rs, _ = make_runs(form)
+        for _ in range(args.warmup):
+            step(rs)
+        ms_f, _ = timed(args.steps, 0, rs)
+        ms_fs, _ = timed(k_serial, "serial", rs)
+        w2 = sum(cwt.cwt_plan_get_timing(r[4])["wide2"][0] for r in rs) / k_serial
+        for r in rs:
+            cwt.cwt_plan_set_timing(r[4], False)
+        err = 0.0
+        for r, r32 in zip(rs, runs):
+            d = torch.linalg.vector_norm((r[5] - r32[5]).reshape(-1)) / torch.linalg.vector_norm(r32[5].reshape(-1))
+            err = max(err, float(d))
+        prec[form] = {"ms_per_step": ms_f / args.steps, "value": units_per_step * args.steps / (ms_f * 1e-3),
+                      "speedup_vs_fp32": total_ms / ms_f,
+                      "wide2_ms_per_step_serialised": w2,
+                      "wide2_speedup_vs_fp32": (cls_tot["wide2"][0] / k_serial) / w2 if w2 > 0 and "wide2" in cls_tot
+                      else None,
+                      "rel_l2_vs_fp32_max_over_transforms": err}
+        for r in rs:
+            r[4].close()
+        del rs
+        torch.cuda.empty_cache()
+
     fftb = None
     if rank == 0 and world == 1 and not args.no_fft_baseline:
         per = []
@@ -738,6 +773,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fft_library_baseline": fftb,
+            "precision_forms": prec or None,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

@@ -86,6 +86,28 @@ typedef enum {
 
 typedef enum { CWT_INPUT_F32 = 0, CWT_INPUT_F64 = 1 } cwt_input_dtype;
 
+/* Arithmetic of the inverse transforms' 1024-point DFT stages (the second pass
+ * of the wide-band scales, Eq. 9 for M >= 2^14 up to 2^23).  FP32: CUDA-core
+ * FFT stages in FP32.  The other forms run each 1024-point DFT as two
+ * 32-point DFT-matrix products on the tensor cores (warp-level MMA) with FP32
+ * accumulation, FP32 twiddles between them, and these operands:
+ *   FP16   - FP16 operands; each 1024-sample column is scaled by a power of two
+ *            into FP16's range (about 3e-4 relative error per stage);
+ *   BF16   - BF16 operands (about 2e-3 relative error per stage);
+ *   FP16X3 - hi + lo FP16 pairs with three products per block (hi*hi, lo*hi,
+ *            hi*lo), about 2^-22 per stage (columns scaled as for FP16);
+ *   BF16X3 - hi + lo BF16 pairs, three products per block, about 2^-16.
+ * Every other kernel (forward transform, band kernels, first pass, power)
+ * stays FP32.  The spectrum product and the FP64-generated tables are the
+ * same for every form. */
+typedef enum {
+    CWT_PRECISION_FP32 = 0,
+    CWT_PRECISION_FP16 = 1,
+    CWT_PRECISION_BF16 = 2,
+    CWT_PRECISION_FP16X3 = 3,
+    CWT_PRECISION_BF16X3 = 4
+} cwt_precision;
+
 /* Plan options.  Fill with cwt_plan_opts_default() and change fields. */
 typedef struct {
     double omega0;       /* Morlet centre wavenumber (default 6) */
@@ -105,6 +127,8 @@ typedef struct {
                             the output's size and runs the transform a few times. 0: no tuning */
     int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
                             (0: 32 MiB; at most 2^36) */
+    int32_t precision;   /* cwt_precision of the 1024-point DFT stages (default CWT_PRECISION_FP32) */
+    int32_t pad_;        /* reserved, 0 */
 } cwt_plan_opts;
 
 void cwt_plan_opts_default(cwt_plan_opts* opts);
@@ -243,9 +267,11 @@ cwt_status cwt_plan_get_timing(cwt_plan* plan, int32_t kernel_class, double* tot
  *
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture on the device.  W_dev and spectrum_dev are device pointers of
- * the current device, 4 B (f32) / 8 B (complex64, spectrum) aligned; N >= 1,
- * n_scales >= 1, otherwise CWT_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+ * stream capture on the device.  W_dev and spectrum_dev must be device memory
+ * (cudaMalloc, torch tensors) of the current device, checked with
+ * cudaPointerGetAttributes; 4 B (f32) / 8 B (complex64, spectrum) aligned;
+ * N >= 1, n_scales >= 1, otherwise CWT_ERR_INVALID_ARG.  Asynchronous on
+ * `stream`. */
 #define CWT_NOALLOC_MAX_PARTIALS 65536
 #define CWT_NOALLOC_CHUNK 32768
 cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, int32_t n_scales, int32_t is_complex,

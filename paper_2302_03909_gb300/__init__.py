@@ -32,6 +32,7 @@ WAVELETS = {"gdw": 0, "mexhat": 0, "morlet": 1, "cbsw": 2, "cwgdw": 3}
 BOUNDARIES = {"periodic": 0, "zero": 1}
 SCALE_UNITS = {"dilation": 0, "w_tilde": 1}
 INPUT_DTYPES = {"f32": 0, "f64": 1}
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16x3": 3, "bf16x3": 4}
 
 # every symbol include/cwt.h declares
 ABI_FUNCTIONS = [
@@ -51,7 +52,8 @@ class _Opts(ctypes.Structure):
                 ("scale_unit", ctypes.c_int32), ("input_dtype", ctypes.c_int32),
                 ("fft_len", ctypes.c_int64), ("eps_trunc", ctypes.c_double),
                 ("min_ctas", ctypes.c_int32), ("tune", ctypes.c_int32),
-                ("wide_batch_bytes", ctypes.c_int64)]
+                ("wide_batch_bytes", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class CwtError(RuntimeError):
@@ -191,7 +193,8 @@ class Plan:
 def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "periodic", *,
                     omega0: float = 6.0, dx: float = 1.0, scale_unit: str = "dilation",
                     input_dtype: str = "f32", fft_len: int = 0, eps_trunc: float = 1e-10,
-                    min_ctas: int = 0, tune: bool = False, wide_batch_bytes: int = 0) -> Plan:
+                    min_ctas: int = 0, tune: bool = False, wide_batch_bytes: int = 0,
+                    precision: str = "fp32") -> Plan:
     lib = load_library()
     sc = np.ascontiguousarray(scales, dtype=np.float64)
     opts = _Opts()
@@ -204,6 +207,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     opts.min_ctas = int(min_ctas)
     opts.tune = 1 if tune else 0
     opts.wide_batch_bytes = int(wide_batch_bytes)
+    opts.precision = PRECISIONS[precision]
     h = ctypes.c_void_p()
     st = lib.cwt_plan_create_ex(ctypes.byref(h), int(N),
                                 sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sc),
@@ -211,7 +215,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     _check(st)
     return Plan(h, int(N), len(sc), wavelet, boundary,
                 dict(omega0=omega0, dx=dx, scale_unit=scale_unit, input_dtype=input_dtype,
-                     fft_len=fft_len, eps_trunc=eps_trunc))
+                     fft_len=fft_len, eps_trunc=eps_trunc, precision=precision))
 
 
 def cwt_plan_get_opts(plan: Plan) -> dict:
@@ -353,8 +357,11 @@ def cwt_wavelet_power_noalloc(W, spectrum, stream=None):
     S, N = W.shape
     if spectrum.dtype != torch.float64 or spectrum.numel() != S:
         raise ValueError("spectrum must hold n_scales float64 values")
-    st = load_library().cwt_wavelet_power_noalloc(_dev_ptr(W, "W"), N, S, int(W.dtype == torch.complex64),
-                                                  _dev_ptr(spectrum, "spectrum"), _stream_ptr(stream))
+    if W.device != spectrum.device:
+        raise ValueError(f"W is on {W.device}, spectrum on {spectrum.device}: both must be on one device")
+    with torch.cuda.device(W.device):
+        st = load_library().cwt_wavelet_power_noalloc(_dev_ptr(W, "W"), N, S, int(W.dtype == torch.complex64),
+                                                      _dev_ptr(spectrum, "spectrum"), _stream_ptr(stream))
     if st == 2:
         need = S * -(-N // NOALLOC_CHUNK)
         raise CwtError(st, f"{need} partial sums needed, the static scratch holds {NOALLOC_MAX_PARTIALS}")

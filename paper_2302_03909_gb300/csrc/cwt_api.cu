@@ -19,6 +19,7 @@
 #include "../../include/cwt.h"
 #include "cwt_kernels.cuh"
 #include "cwt_tables.cuh"
+#include "cwt_tc.cuh"
 #include "cwt_plan_impl.h"
 
 using namespace cwtk;
@@ -51,6 +52,7 @@ const Tables& tables() {
         fill_p1_tables(x);
         fill_wide_tables(x);
         fill_fwd_tables(x);
+        fill_tc_tables(x);
         return x;
     }();
     return t;
@@ -503,6 +505,17 @@ void scale_band(const cwt_plan* p, double wt, double u_lo, double u_hi, int64_t*
 
 size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_stride(T) * sizeof(float2); }
 
+// Pass 2 of the wide scales: the FP32 CUDA-core kernel, or with a reduced
+// precision (opts.precision) and L = 1024 the tensor-core kernel (cwt_tc.cuh)
+bool wide2_on_tc(const cwt_plan* p) { return p->opts.precision != CWT_PRECISION_FP32 && p->wide_logl == 10; }
+const Entry& wide2_entry(const cwt_plan* p) {
+    const Tables& tb = tables();
+    return wide2_on_tc(p) ? tb.wide2_tc[p->opts.precision][p->crop] : tb.wide2[p->wide_logl][p->crop];
+}
+size_t wide2_smem(const cwt_plan* p) {
+    return wide2_on_tc(p) ? tc_smem_bytes(p->opts.precision) : stage_smem(p->wide_logl, wide2_entry(p).T);
+}
+
 cwt_status opt_in_smem(cwt_plan* p, const void* fn);
 
 cwt_status build_plan(cwt_plan* p) {
@@ -608,7 +621,19 @@ cwt_status build_plan(cwt_plan* p) {
         const int T2 = tb.wide2[p->wide_logl][0].T;
         p->wide_G = (int)std::max<int64_t>(1, p->opts.wide_batch_bytes / (int64_t)((size_t)M * sizeof(float2)));
         const int64_t tiles_job = (A + T2 - 1) / T2;
-        p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()), p->opts.min_ctas);
+        if (wide2_on_tc(p)) {
+            // the tensor-core pass 2 is resident as 2 CTAs per SM (single products) or
+            // 1 (hi + lo): about that many CTAs per launch, each looping over its
+            // tiles so that its set-up is paid once
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+            const int res = sms * (p->opts.precision == CWT_PRECISION_FP16X3 ||
+                                   p->opts.precision == CWT_PRECISION_BF16X3 ? 1 : 2);
+            const int64_t per = std::max<int64_t>(1, res / std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
+            p->wide_D = (int)((tiles_job + per - 1) / per);
+        } else {
+            p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()), p->opts.min_ctas);
+        }
         const int ntiles2 = (int)((tiles_job + p->wide_D - 1) / p->wide_D);
         const int L = 1 << p->wide_logl;
         for (size_t i = 0; i < wide.size(); i++) {
@@ -726,7 +751,7 @@ cwt_status build_plan(cwt_plan* p) {
     for (const auto& wb : p->wide) {
         fns.push_back(wb.logl1 < 0 ? (const void*)tb.wide1[p->wide_loga].fn
                                    : (const void*)tb.wide1p[wb.logl1][wb.var].fn);
-        fns.push_back((const void*)tb.wide2[p->wide_logl][p->crop].fn);
+        fns.push_back((const void*)wide2_entry(p).fn);
     }
     for (const void* f : fns) {
         if (!f) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
@@ -1017,7 +1042,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         const auto& wb = p->wide[wi];
         const int si = next++ % nstreams;
         cudaStream_t ws = streams[si];
-        const Entry& e2 = tb.wide2[p->wide_logl][p->crop];
+        const Entry& e2 = wide2_entry(p);
         const int L = 1 << p->wide_logl;
         Params Q = P;
         Q.job0 = wb.job0;
@@ -1048,7 +1073,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         }
         Q.D = p->wide_D;
         const int tiles2 = (Q.A + e2.T - 1) / e2.T;
-        if ((st = launch(p, e2, dim3((tiles2 + Q.D - 1) / Q.D, wb.count), stage_smem(p->wide_logl, e2.T), Q, ws,
+        if ((st = launch(p, e2, dim3((tiles2 + Q.D - 1) / Q.D, wb.count), wide2_smem(p), Q, ws,
                          CWT_KCLASS_WIDE2, wb.out_bytes)) != CWT_OK)
             return st;
     }
@@ -1424,6 +1449,8 @@ void cwt_plan_opts_default(cwt_plan_opts* o) {
     o->min_ctas = 0;
     o->tune = 0;
     o->wide_batch_bytes = 0;
+    o->precision = CWT_PRECISION_FP32;
+    o->pad_ = 0;
 }
 
 cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
@@ -1452,7 +1479,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     for (int32_t i = 0; i < n_scales; i++)
         if (!std::isfinite(scales[i]) || !(scales[i] > 0.0)) return CWT_ERR_INVALID_ARG;
     if (o.min_ctas < 0 || o.min_ctas > (1 << 20) || o.wide_batch_bytes < 0 ||
-        o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1))
+        o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1) ||
+        o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3)
         return CWT_ERR_INVALID_ARG;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;

@@ -38,6 +38,18 @@ cwt_status scratch_address(double** out) {
     return CWT_OK;
 }
 
+// True if q is device memory of the device `dev` (cudaPointerGetAttributes
+// allocates nothing).  A pointer of another device, or host memory, would
+// make the kernels read or write memory this device cannot address.
+bool on_device(const void* q, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, int32_t n_scales,
@@ -47,6 +59,9 @@ extern "C" cwt_status cwt_wavelet_power_noalloc(const void* W_dev, int64_t N, in
         return CWT_ERR_INVALID_ARG;
     const int64_t chunks = (N + CWT_NOALLOC_CHUNK - 1) / CWT_NOALLOC_CHUNK;
     if (chunks * (int64_t)n_scales > CWT_NOALLOC_MAX_PARTIALS || n_scales > 65535) return CWT_ERR_UNSUPPORTED;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CWT_ERR_CUDA;
+    if (!on_device(W_dev, dev) || !on_device(spectrum_dev, dev)) return CWT_ERR_INVALID_ARG;
     double* partials = nullptr;
     cwt_status st = scratch_address(&partials);
     if (st != CWT_OK) return st;

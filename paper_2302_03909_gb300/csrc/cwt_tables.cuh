@@ -57,11 +57,13 @@ struct Tables {
     Entry wide2[kLmaxLog + 1][2];           // [log2 L][crop]
     Entry fwd2[kLmaxLog + 1];
     EntryP wide1p[kLmaxLog + 1][kP1Var];    // [log2 L1][column-count variant]
+    Entry wide2_tc[5][2];                   // pass 2 with L = 1024 on the tensor cores: [precision][crop]
 };
 
 void fill_band_tables(Tables& t);   // cwt_tab_band.cu
 void fill_p1_tables(Tables& t);     // cwt_tab_p1.cu
 void fill_wide_tables(Tables& t);   // cwt_tab_wide.cu
 void fill_fwd_tables(Tables& t);    // cwt_tab_fwd.cu
+void fill_tc_tables(Tables& t);     // cwt_tab_tc.cu
 
 }  // namespace cwtk

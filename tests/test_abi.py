@@ -116,11 +116,26 @@ def test_plan_options_struct_matches_the_header(cwt):
     the defaults the library fills in."""
     o = cwt._Opts()
     cwt.load_library().cwt_plan_opts_default(ctypes.byref(o))
-    assert ctypes.sizeof(o) == 56
+    assert ctypes.sizeof(o) == 64
     assert (o.omega0, o.dx, o.scale_unit, o.input_dtype, o.fft_len) == (6.0, 1.0, 0, 0, 0)
     assert (o.eps_trunc, o.min_ctas, o.tune, o.wide_batch_bytes) == (1e-10, 0, 0, 0)
+    assert (o.precision, o.pad_) == (0, 0)
     with open(os.path.join(ROOT, "include", "cwt.h")) as fh:
         text = fh.read()
     body = text[text.index("typedef struct {", text.index("cwt_input_dtype;")):text.index("} cwt_plan_opts;")]
     fields = re.findall(r"^\s+(?:double|int32_t|int64_t)\s+(\w+);", body, flags=re.M)
     assert fields == [name for name, _ in cwt._Opts._fields_]
+
+
+def test_precision_option_range_checked_on_the_host(cwt):
+    """cwt_precision values outside FP32 .. BF16X3 are refused before any CUDA call."""
+    lib = cwt.load_library()
+    o = cwt._Opts()
+    lib.cwt_plan_opts_default(ctypes.byref(o))
+    sc = (ctypes.c_double * 1)(4.0)
+    h = ctypes.c_void_p()
+    for bad in (-1, 5):
+        o.precision = bad
+        assert lib.cwt_plan_create_ex(ctypes.byref(h), 1024, sc, 1, 0, 0, ctypes.byref(o)) == 1
+        assert h.value is None
+    assert cwt.PRECISIONS == {"fp32": 0, "fp16": 1, "bf16": 2, "fp16x3": 3, "bf16x3": 4}
