@@ -122,11 +122,12 @@ typedef struct {
     int32_t min_ctas;    /* launch shape: the W-writing launches take up to 8 tiles per CTA while
                             keeping at least this many CTAs (0: 304, two per SM; at most 2^20) */
     int32_t tune;        /* 1: at creation, time plans with min_ctas in {152, 304, 608} and
-                            wide_batch_bytes in {16, 32} MiB (a nonzero value given above is kept)
-                            on this device and keep the fastest.  Needs temporary device memory of
-                            the output's size and runs the transform a few times. 0: no tuning */
+                            wide_batch_bytes in {16, 32} MiB ({64, 128, 256} MiB with a reduced
+                            precision) (a nonzero value given above is kept) on this device and keep
+                            the fastest.  Needs temporary device memory of the output's size and runs
+                            the transform a few times. 0: no tuning */
     int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
-                            (0: 32 MiB; at most 2^36) */
+                            (0: 32 MiB, 128 MiB with a reduced precision; at most 2^36) */
     int32_t precision;   /* cwt_precision of the 1024-point DFT stages (default CWT_PRECISION_FP32) */
     int32_t pad_;        /* reserved, 0 */
 } cwt_plan_opts;

@@ -31,6 +31,9 @@ constexpr int kMaxLogM = 25;           // M <= 2^25 (zero boundary of N = 2^24)
 constexpr int kBandMaxLog = 10;        // band kernels up to L = 1024 when M > kLmax
 constexpr int kWideLog = 10;           // pass-2 DFT length of wide scales (M <= 2^23)
 constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide launch; one per stream
+// the tensor-core pass 2 (reduced precision) pays a fill and drain per launch:
+// larger launches (more tiles per CTA) by default
+constexpr size_t kWideBatchBytesTc = size_t(128) << 20;
 
 // ----------------------------------------------------------- launch shapes
 
@@ -466,7 +469,25 @@ void free_plan(cwt_plan* p) {
     if (p->child) free_plan(p->child);
     for (cwt_plan* q : p->subs) free_plan(q);
     if (p->d_ext) cudaFree(p->d_ext);
+    if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (EncodeTiledFn)f;
+    }();
+    return fn;
 }
 
 double out_row_bytes(const cwt_plan* p) {
@@ -508,13 +529,7 @@ size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_st
 // Pass 2 of the wide scales: the FP32 CUDA-core kernel, or with a reduced
 // precision (opts.precision) and L = 1024 the tensor-core kernel (cwt_tc.cuh)
 bool wide2_on_tc(const cwt_plan* p) { return p->opts.precision != CWT_PRECISION_FP32 && p->wide_logl == 10; }
-const Entry& wide2_entry(const cwt_plan* p) {
-    const Tables& tb = tables();
-    return wide2_on_tc(p) ? tb.wide2_tc[p->opts.precision][p->crop] : tb.wide2[p->wide_logl][p->crop];
-}
-size_t wide2_smem(const cwt_plan* p) {
-    return wide2_on_tc(p) ? tc_smem_bytes(p->opts.precision) : stage_smem(p->wide_logl, wide2_entry(p).T);
-}
+const Entry& wide2_entry(const cwt_plan* p) { return tables().wide2[p->wide_logl][p->crop]; }
 
 cwt_status opt_in_smem(cwt_plan* p, const void* fn);
 
@@ -622,14 +637,12 @@ cwt_status build_plan(cwt_plan* p) {
         p->wide_G = (int)std::max<int64_t>(1, p->opts.wide_batch_bytes / (int64_t)((size_t)M * sizeof(float2)));
         const int64_t tiles_job = (A + T2 - 1) / T2;
         if (wide2_on_tc(p)) {
-            // the tensor-core pass 2 is resident as 2 CTAs per SM (single products) or
-            // 1 (hi + lo): about that many CTAs per launch, each looping over its
-            // tiles so that its set-up is paid once
+            // the tensor-core pass 2 is resident as one CTA per SM: about one CTA per
+            // SM per launch, each looping over its tiles (set-up paid once, the next
+            // tile's copy in flight during the current tile's work)
             int sms = 152;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-            const int res = sms * (p->opts.precision == CWT_PRECISION_FP16X3 ||
-                                   p->opts.precision == CWT_PRECISION_BF16X3 ? 1 : 2);
-            const int64_t per = std::max<int64_t>(1, res / std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
+            const int64_t per = std::max<int64_t>(1, sms / std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
             p->wide_D = (int)((tiles_job + per - 1) / per);
         } else {
             p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()), p->opts.min_ctas);
@@ -703,6 +716,23 @@ cwt_status build_plan(cwt_plan* p) {
     if (!p->wide.empty())
         ycount = std::max(ycount, p->y_stride * (size_t)std::min<size_t>(p->wide.size(), cwt_plan::kSide + 1));
     if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
+    if (!p->wide.empty() && wide2_on_tc(p)) {
+        // Y as float rows: [slab][1024 rows][2 A floats]; boxes of 256 rows x 8 complex
+        // columns land in shared memory with the 64-byte swizzle the kernel reads
+        EncodeTiledFn enc = encode_tiled();
+        if (!enc) return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        const int64_t A = M >> p->wide_logl;
+        const cuuint64_t dims[3] = {(cuuint64_t)(2 * A), 1024, (cuuint64_t)(ycount / (size_t)M)};
+        const cuuint64_t strides[2] = {(cuuint64_t)(A * 8), (cuuint64_t)(M * 8)};
+        const cuuint32_t box[3] = {16, 256, 1}, estr[3] = {1, 1, 1};
+        if (enc(&p->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->d_Y, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        CWT_CUDA(p, cudaHostAlloc((void**)&p->h_err, sizeof(int32_t), cudaHostAllocMapped));
+        *p->h_err = 0;
+        CWT_CUDA(p, cudaHostGetDevicePointer((void**)&p->d_err, p->h_err, 0));
+    }
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
     if (p->child) {
         std::vector<EdgeRow> er(p->child_n);
@@ -751,7 +781,12 @@ cwt_status build_plan(cwt_plan* p) {
     for (const auto& wb : p->wide) {
         fns.push_back(wb.logl1 < 0 ? (const void*)tb.wide1[p->wide_loga].fn
                                    : (const void*)tb.wide1p[wb.logl1][wb.var].fn);
-        fns.push_back((const void*)wide2_entry(p).fn);
+        if (wide2_on_tc(p)) {
+            fns.push_back((const void*)tb.wide2_tc[p->opts.precision][p->crop].fn);
+            fns.push_back((const void*)tb.wide2_tc[p->opts.precision][p->crop].gfn);
+        } else {
+            fns.push_back((const void*)wide2_entry(p).fn);
+        }
     }
     for (const void* f : fns) {
         if (!f) return fail(p, CWT_ERR_INTERNAL, "missing kernel instantiation");
@@ -1048,6 +1083,8 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         Q.job0 = wb.job0;
         Q.A = (int32_t)(p->M >> p->wide_logl);
         Q.Y = p->d_Y + (size_t)si * p->y_stride;
+        const bool tc = wide2_on_tc(p);
+        Q.yperm = tc ? 1 : 0;                    // Y rows in the tensor-core pass 2's order
         if (wb.logl1 < 0) {
             const Entry& e1 = tb.wide1[p->wide_loga];
             if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T, wb.count), stage_smem(p->wide_loga, e1.T), Q, ws,
@@ -1073,9 +1110,25 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         }
         Q.D = p->wide_D;
         const int tiles2 = (Q.A + e2.T - 1) / e2.T;
-        if ((st = launch(p, e2, dim3((tiles2 + Q.D - 1) / Q.D, wb.count), wide2_smem(p), Q, ws,
-                         CWT_KCLASS_WIDE2, wb.out_bytes)) != CWT_OK)
+        const dim3 grid2((tiles2 + Q.D - 1) / Q.D, wb.count);
+        if (tc) {
+            const TcEntry& te = tb.wide2_tc[p->opts.precision][p->crop];
+            Q.yz0 = (int32_t)((size_t)si * p->y_stride / (size_t)p->M);
+            Q.err = p->d_err;
+            if (!te.fn || !te.gfn) return fail(p, CWT_ERR_INTERNAL, "missing tensor-core pass-2 instantiation");
+            if (p->rec) {
+                rec_launch(p, (const void*)te.gfn, grid2, dim3(kTcThreads), tc_smem_bytes(p->opts.precision), ws, Q);
+            } else {
+                if ((st = opt_in_smem(p, (const void*)te.fn)) != CWT_OK) return st;
+                LaunchTimer lt(p, CWT_KCLASS_WIDE2, wb.out_bytes, ws);
+                te.fn<<<grid2, te.NT, tma_smem_bytes(p->opts.precision), ws>>>(Q, p->ymap);
+                CWT_CUDA(p, cudaGetLastError());
+                lt.done();
+            }
+        } else if ((st = launch(p, e2, grid2, stage_smem(p->wide_logl, e2.T), Q, ws, CWT_KCLASS_WIDE2,
+                                wb.out_bytes)) != CWT_OK) {
             return st;
+        }
     }
     for (size_t gi = 0; gi < p->groups.size(); gi++) {
         const auto& g = p->groups[gi];
@@ -1113,7 +1166,21 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
 // replayed while (signal, W, spectrum) repeat.  Direct launches when timing is
 // on, on the legacy default stream, inside a caller's own capture, or if
 // capture is unavailable.
+// A tensor-core pass 2 of an earlier call (this plan or one of its sub-plans)
+// whose bounded wait for a TMA copy gave up: reported once, as CWT_ERR_TIMEOUT.
+bool take_timeout(cwt_plan* p) {
+    bool t = false;
+    if (p->h_err && *(volatile int32_t*)p->h_err) {
+        *(volatile int32_t*)p->h_err = 0;
+        t = true;
+    }
+    if (p->child) t |= take_timeout(p->child);
+    for (cwt_plan* q : p->subs) t |= take_timeout(q);
+    return t;
+}
+
 cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
+    if (take_timeout(p)) return fail(p, CWT_ERR_TIMEOUT, "a tensor-core pass 2 of an earlier call gave up waiting");
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (p->timing || !p->graphs_ok || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread ||
         cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
@@ -1360,7 +1427,9 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
     struct Cand { int32_t ctas; int64_t wb; };
     std::vector<Cand> cands;
     for (int32_t c : {152 * 2, 152, 152 * 4})
-        for (int64_t wb : {int64_t(32) << 20, int64_t(16) << 20}) {
+        for (int64_t wb : o.precision == CWT_PRECISION_FP32
+                              ? std::initializer_list<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
+                              : std::initializer_list<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20}) {
             const Cand k{o.min_ctas ? o.min_ctas : c, o.wide_batch_bytes ? o.wide_batch_bytes : wb};
             bool dup = false;
             for (const Cand& q : cands) dup |= q.ctas == k.ctas && q.wb == k.wb;
@@ -1484,7 +1553,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         return CWT_ERR_INVALID_ARG;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;
-    if (o.wide_batch_bytes == 0) o.wide_batch_bytes = (int64_t)kWideBatchBytes;
+    if (o.wide_batch_bytes == 0)
+        o.wide_batch_bytes = (int64_t)(o.precision == CWT_PRECISION_FP32 ? kWideBatchBytes : kWideBatchBytesTc);
 
     int64_t M;
     if (boundary == CWT_BOUNDARY_PERIODIC) {

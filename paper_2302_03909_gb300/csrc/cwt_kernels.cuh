@@ -90,7 +90,14 @@ struct Params {
     float half_w0sq;         // omega0^2 / 2
     float corr_v2;           // Morlet: the correction e^{-(v^2 + omega0^2)/2} is below the band
                              // truncation threshold for v^2 >= corr_v2
+    int32_t yperm;           // wide pass 1: Y rows in the order of the tensor-core pass 2 (tc_rho)
+    int32_t yz0;             // tensor-core pass 2: index of this launch's first Y slab in the plan's Y
+    int32_t* err;            // tensor-core pass 2: set to 1 when a bounded wait gives up
 };
+
+// Rows of the wide-scale intermediate in the order the tensor-core pass 2
+// reads them (L = 1024): bits 1-2 and 6-7 of the row index swapped (an involution).
+__host__ __device__ constexpr int tc_rho(int b) { return (b & ~0xC6) | ((b & 0x06) << 5) | ((b & 0xC0) >> 5); }
 
 // Block coordinates of a CTA within its launch.  A plain launch takes them from
 // blockIdx and gridDim.  A grouped launch merges the launches of one kernel
@@ -700,7 +707,7 @@ struct YOut {
         const uint32_t b = (uint32_t)(COLS_B ? b0 + t : b0);
         const uint32_t d1 = (uint32_t)(COLS_B ? 0 : d0 + t);
         const uint32_t mask = (uint32_t)(p->M - 1);
-        float2* row = Y + (int64_t)b * A;
+        float2* row = Y + (int64_t)(p->yperm ? (uint32_t)tc_rho((int)b) : b) * A;
         const uint64_t pol = l2_policy_keep();
         const uint32_t dj = d1 + (uint32_t)A1 * (uint32_t)j;
         constexpr int CH = R >= 8 ? 4 : 1;                 // interleaved recurrences

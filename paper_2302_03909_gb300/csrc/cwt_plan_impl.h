@@ -2,6 +2,7 @@
 // (planner and launches in cwt_api.cu, statistics of W in cwt_stats.cu).
 // Not part of the C ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -142,6 +143,12 @@ struct cwt_plan {
     void* d_ext = nullptr;                // N + 2 ext_E samples, the input's dtype
 
     Recorder* rec = nullptr;              // set while a batch records this plan's launches
+
+    // tensor-core pass 2 (opts.precision != FP32, L = 1024): TMA map of Y, and a
+    // flag in mapped host memory that its kernel sets when a bounded wait gives up
+    CUtensorMap ymap{};
+    int32_t* h_err = nullptr;             // host view (cudaHostAlloc, mapped)
+    int32_t* d_err = nullptr;             // device view
 
     std::string err;
 };

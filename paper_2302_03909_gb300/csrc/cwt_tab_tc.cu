@@ -5,7 +5,7 @@
 namespace cwtk {
 
 template <int FORM, bool CROP>
-static Entry tc_entry() { return {k_wide2_tc<FORM, CROP>, k_wide2_tc_g<FORM, CROP>, kTcCols, kTcThreads, 10}; }
+static TcEntry tc_entry() { return {k_wide2_tma<FORM, CROP>, k_wide2_tc_g<FORM, CROP>, tma_threads(FORM)}; }
 
 void fill_tc_tables(Tables& t) {
     t.wide2_tc[TC_FP16][0] = tc_entry<TC_FP16, false>();

@@ -4,6 +4,8 @@
 // the template instantiations in parallel.
 #pragma once
 
+#include <cuda.h>
+
 #include <utility>
 
 #include "cwt_kernels.cuh"
@@ -34,6 +36,10 @@ using KernFnG = void (*)(GroupMap);
 struct Entry { KernFn fn; KernFnG gfn; int T, NT, logl; };
 using KernFnP = void (*)(Wide1pArgs);
 struct EntryP { KernFnP fn; KernFnG gfn; int T, NT, logl; };
+// tensor-core pass 2: fn takes the TMA map of the plan's Y and runs NT threads
+// (plain launches); gfn is the grouped form (kTcThreads threads, cp.async)
+using KernFnTma = void (*)(Params, CUtensorMap);
+struct TcEntry { KernFnTma fn; KernFnG gfn; int NT; };
 
 template <int LOGL, int T, bool CROP, int RD = 1>
 Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, k_band_g<LOGL, T, CROP, RD>, T, T * col_threads(LOGL), LOGL}; }
@@ -57,7 +63,7 @@ struct Tables {
     Entry wide2[kLmaxLog + 1][2];           // [log2 L][crop]
     Entry fwd2[kLmaxLog + 1];
     EntryP wide1p[kLmaxLog + 1][kP1Var];    // [log2 L1][column-count variant]
-    Entry wide2_tc[5][2];                   // pass 2 with L = 1024 on the tensor cores: [precision][crop]
+    TcEntry wide2_tc[5][2];                 // pass 2 with L = 1024 on the tensor cores: [precision][crop]
 };
 
 void fill_band_tables(Tables& t);   // cwt_tab_band.cu
