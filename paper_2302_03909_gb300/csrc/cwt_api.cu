@@ -458,7 +458,7 @@ void free_plan(cwt_plan* p) {
     if (p->ev_pre) cudaEventDestroy(p->ev_pre);
     if (p->ev_pfwd) cudaEventDestroy(p->ev_pfwd);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Zt, p->d_Y,
+    void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
@@ -624,8 +624,6 @@ cwt_status build_plan(cwt_plan* p) {
             g.ntiles += per_job;
             assign_parts(J, per_job);
             g.bytes += job_rows(J) * out_row_bytes(p) + 8.0 * J.K;
-            J.zt_off = (int32_t)p->zt_count;
-            p->zt_count += J.K;
             p->jobs.push_back(J);
         }
         p->groups.push_back(g);
@@ -708,7 +706,6 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tw_tab, tt)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
-    if ((st = dev_alloc(p, &p->d_Zt, (size_t)p->zt_count)) != CWT_OK) return st;
     if (!p->wide.empty() && (st = dev_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
     size_t ycount = 0;
     if (!small) ycount = (size_t)M;
@@ -800,7 +797,6 @@ Params base_params(const cwt_plan* p) {
     P.Fp = p->d_Fp;
     P.Fp_out = p->d_Fp;
     P.Ft = p->d_Ft;
-    P.Zt = p->d_Zt;
     P.Y = p->d_Y;
     P.partials = p->d_partials;
     P.tw_lo = p->d_tw_lo;
@@ -1019,18 +1015,6 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, fs,
                          CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
             return st;
-    }
-
-    // the band jobs' values Z(k), once per call (each band CTA reads its job's table)
-    if (p->n_band_jobs > 0) {
-        LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, fs);
-        if (p->rec) {
-            rec_launch(p, (const void*)k_band_table_g, dim3((unsigned)p->n_band_jobs), dim3(256), 0, fs, P);
-        } else {
-            k_band_table<<<(unsigned)p->n_band_jobs, 256, 0, fs>>>(P);
-            CWT_CUDA(p, cudaGetLastError());
-            lt.done();
-        }
     }
 
     // the wide scales' pass 1 reads the spectrum column by column: transpose it once
@@ -1426,10 +1410,11 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
                         int32_t boundary, const cwt_plan_opts& o) {
     struct Cand { int32_t ctas; int64_t wb; };
     std::vector<Cand> cands;
+    const std::vector<int64_t> wb_cands =
+        o.precision == CWT_PRECISION_FP32 ? std::vector<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
+                                          : std::vector<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20};
     for (int32_t c : {152 * 2, 152, 152 * 4})
-        for (int64_t wb : o.precision == CWT_PRECISION_FP32
-                              ? std::initializer_list<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
-                              : std::initializer_list<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20}) {
+        for (int64_t wb : wb_cands) {
             const Cand k{o.min_ctas ? o.min_ctas : c, o.wide_batch_bytes ? o.wide_batch_bytes : wb};
             bool dup = false;
             for (const Cand& q : cands) dup |= q.ctas == k.ctas && q.wb == k.wb;

@@ -61,12 +61,11 @@ struct Job {
     int32_t k_lo;       // signed lowest bin of the band
     int32_t K;          // band width in bins (1..M)
     int32_t tile0;      // first tile of this job within its launch
-    int32_t zt_off;     // band jobs: offset of the job's band values Z(k_lo + i) in Params::Zt
+    int32_t pad_;
 };
 
 struct Params {
     const float2* Fp;        // F(m) = sum_n f(n) e^{+2 pi i m n / M}, m in [0, M/2]
-    const float2* Zt;        // band jobs' values Z(k_lo + i), i < K, computed once per call
     const float2* Ft;        // wide pass 1: Ft[b A + a] = F(k), k = b + L a over all M unsigned bins
     float2* Fp_out;          // forward pass sink
     float2* Y;               // pass-1 -> pass-2 intermediate, [job][b][d]
@@ -628,8 +627,10 @@ __device__ __forceinline__ void band_body(const Params& p, const Cta c) {
     __syncthreads();
     const Job& J = sJ;
     const int dbase = (tile - J.tile0) * T * p.D;
+    // the job's band values Z(k) = F(k) amp psi_hat(alpha k), generated here from the
+    // spectrum (Eq. 10) into shared memory: no per-scale product goes to global memory
     for (int i = threadIdx.x; i < RD * L; i += NT)
-        Zs[i] = i < J.K ? __ldg(&p.Zt[J.zt_off + i]) : make_float2(0.f, 0.f);
+        Zs[i] = i < J.K ? band_value(p, J, J.k_lo + i) : make_float2(0.f, 0.f);
     WOut<CROP> out = make_wout<CROP>(p, J, dbase);
 #pragma unroll 1
     for (int q = 0; q < p.D; q++) {
@@ -654,21 +655,6 @@ __global__ void __launch_bounds__(T * col_threads(LOGL, MAXLR), min_blocks(T * c
     Cta c;
     const Params& p = group_args<Params>(g, c);
     band_body<LOGL, T, CROP, RD, MAXLR>(p, c);
-}
-
-// The band values of every band job, once per call: grid = band jobs.
-__device__ __forceinline__ void band_table_body(const Params& p, const Cta c) {
-    __shared__ Job sJ;
-    if (threadIdx.x == 0) sJ = p.jobs[c.x];
-    __syncthreads();
-    float2* zt = const_cast<float2*>(p.Zt) + sJ.zt_off;
-    for (int i = threadIdx.x; i < sJ.K; i += 256) zt[i] = band_value(p, sJ, sJ.k_lo + i);
-}
-static __global__ void __launch_bounds__(256) k_band_table(Params p) { band_table_body(p, cta_plain()); }
-static __global__ void __launch_bounds__(256) k_band_table_g(GroupMap g) {
-    Cta c;
-    const Params& p = group_args<Params>(g, c);
-    band_table_body(p, c);
 }
 
 // ------------------------------------------------------------ wide pass 1

@@ -80,8 +80,6 @@ struct cwt_plan {
     int32_t* d_part_cnt = nullptr;
     float2* d_Fp = nullptr;
     float2* d_Ft = nullptr;
-    float2* d_Zt = nullptr;               // band jobs' values, zt_count entries
-    int64_t zt_count = 0;               // transposed full spectrum (plans with wide scales)
     float2* d_Y = nullptr;
     double* d_partials = nullptr;
     float2* d_tw_lo = nullptr;
