@@ -64,6 +64,10 @@ def parse_args():
                     help="skip the comparison with the library FFT (torch.fft / cuFFT) written the usual way")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default run: skip the embedded batch measurement (--batch-signals signals)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default run: skip the embedded serving measurement (a short trace)")
     ap.add_argument("--precisions", default="fp16x3,bf16x3,fp16,bf16",
                     help="tensor-core forms of the 1024-point DFT stages timed beside FP32 (comma list; "
                          "empty: none)")
@@ -401,7 +405,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+def run_serving(args, embedded=False):
     """Poisson arrivals (N = 2^10..2^24, 16..128 scales, GDW or Morlet, periodic or
     zero boundary) served with ``--slots`` streams, then the same trace with one
     slot (serial execution); plans of every request shape are created first
@@ -453,10 +457,12 @@ def run_serving(args):
                        "buffers": "new per request" if args.fresh_buffers
                        else "per plan instance up to 64 MiB (graph replay), new per request above"},
             "data": "synthetic"}
+    if embedded:
+        return line
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, embedded=False):
     """A batch of signals of uneven lengths: N log-uniform in [1024, 65536]
     (integers, mostly not powers of two), 16..96 log-spaced dilations from 2
     (GDW) or 4 (Morlet) to N/4, the wavelet and the boundary 50/50, multi-tone
@@ -539,7 +545,7 @@ def run_batch(args):
     del graph
     for p in plans:
         p.close()
-    cpu = None if args.no_cpu_baseline else batch_cpu_baseline(reqs, args.cpu_seconds)
+    cpu = None if (args.no_cpu_baseline or embedded) else batch_cpu_baseline(reqs, args.cpu_seconds)
     line = {"impl": "ours", "metric": "CWT scale-samples/s, batch of uneven lengths", "unit": "scale-samples/s",
             "higher_is_better": True, "value": units / out["grouped_s"], "graph": units / out["graph_s"],
             "one_by_one": units / out["one_by_one_s"], "cpu_baseline": cpu,
@@ -553,6 +559,8 @@ def run_batch(args):
                                 "graph: one CUDA graph over the per-signal launch sequences; one_by_one: one "
                                 "launch sequence per signal on one stream"},
             "data": "synthetic"}
+    if embedded:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -597,7 +605,11 @@ def run_ours(args):
     runs, subset = make_runs()
     t_plan = time.perf_counter() - t_plan0
     plans = [r[4] for r in runs]
-    shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes")} for p in plans]
+    fft_lens = [p.M for p in plans]
+    transforms = [f"{r[1]}/{r[2]}" for r in runs]
+    boundaries_used = sorted({r[2] for r in runs})
+    shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes", "band_depth")}
+              for p in plans]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step(rs=None):
@@ -743,6 +755,27 @@ def run_ours(args):
         cb = cpu_baseline(args.workload, args.cpu_seconds)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
+    # the batched and served forms on the same GPU in the same run (summaries; --batch and
+    # --serving print the full lines)
+    for p in plans:
+        p.close()
+    plans = []
+    del runs
+    torch.cuda.empty_cache()
+    batch = serving_line = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        b = run_batch(args, embedded=True)
+        batch = {"value": b["value"], "unit": UNIT, "graph": b["graph"], "one_by_one": b["one_by_one"],
+                 "signals": b["config"]["signals"], "scale_samples": b["config"]["scale_samples"],
+                 "grouped_info": b["detail"]["grouped_info"], "what": b["config"]["timed"]}
+    if rank == 0 and world == 1 and not args.no_serving:
+        sv = run_serving(args, embedded=True)
+        serving_line = {k: sv[k] for k in ("p50_ms", "p99_ms", "serial_p50_ms", "serial_p99_ms",
+                                           "offered_scale_samples_per_s")}
+        serving_line["served_scale_samples_per_s"] = sv["concurrent"]["scale_samples_per_s"]
+        serving_line["serial_scale_samples_per_s"] = sv["serial"]["scale_samples_per_s"]
+        serving_line["config"] = sv["config"]
+
     if rank == 0:
         w0 = synth.WORKLOADS[parts[0]]
         wavs = [synth.WORKLOADS[q]["wavelet"] for q in parts]
@@ -753,9 +786,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "n_scales": w0["n_scales"], "wavelets": wavs,
                        **({"omega0": 6.0} if "morlet" in wavs else {}),
-                       "boundaries": sorted({r[2] for r in runs}),
-                       "transforms": [f"{r[1]}/{r[2]}" for r in runs],
-                       "fft_len": [p.M for p in plans], "power_spectrum": True,
+                       "boundaries": boundaries_used,
+                       "transforms": transforms,
+                       "fft_len": fft_lens, "power_spectrum": True,
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "inputs": "resident in HBM", "parallelism": f"replicas x{world}",
                        "launch_shape": shapes, "plan_s": round(t_plan, 3),
@@ -782,6 +815,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fft_library_baseline": fftb,
             "precision_forms": prec or None,
+            "batch": batch,
+            "serving": serving_line,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

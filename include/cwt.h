@@ -123,13 +123,18 @@ typedef struct {
                             keeping at least this many CTAs (0: 304, two per SM; at most 2^20) */
     int32_t tune;        /* 1: at creation, time plans with min_ctas in {152, 304, 608} and
                             wide_batch_bytes in {16, 32} MiB ({64, 128, 256} MiB with a reduced
-                            precision) (a nonzero value given above is kept) on this device and keep
-                            the fastest.  Needs temporary device memory of the output's size and runs
-                            the transform a few times. 0: no tuning */
+                            precision), then band_depth in {4, 2, 1} (a nonzero value given for any of
+                            them is kept) on this device and keep the fastest.  Needs temporary device
+                            memory of the output's size and runs the transform a few times.  If the
+                            environment variable CWT_TUNE_CACHE names a file, a choice stored there for
+                            the same device and plan inputs is used without timing, and new choices are
+                            appended to it (one line each).  0: no tuning */
     int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
                             (0: 32 MiB, 128 MiB with a reduced precision; at most 2^36) */
     int32_t precision;   /* cwt_precision of the 1024-point DFT stages (default CWT_PRECISION_FP32) */
-    int32_t pad_;        /* reserved, 0 */
+    int32_t band_depth;  /* stage fusion: bands of up to band_depth * 1024 bins (1, 2 or 4) are computed in
+                            one pass, the band kernel's first DFT stage filled by a Horner sum of band_depth
+                            terms; wider bands take the two-pass path.  0: 4 (or tuned) */
 } cwt_plan_opts;
 
 void cwt_plan_opts_default(cwt_plan_opts* opts);

@@ -11,6 +11,7 @@
 #include <tuple>
 #include <set>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -583,8 +584,8 @@ cwt_status build_plan(cwt_plan* p) {
         int lk = std::max(1, ilog2(J.K));
         if (small) by_logl[std::min(lk, p->logM)].push_back(J);
         else if (lk <= kBandMaxLog) by_logl[lk].push_back(J);
-        else if (J.K <= (2 << kBandDepthLog)) by_logl[kLmaxLog + 1].push_back(J);
-        else if (J.K <= (4 << kBandDepthLog)) by_logl[kLmaxLog + 2].push_back(J);
+        else if (p->opts.band_depth >= 2 && J.K <= (2 << kBandDepthLog)) by_logl[kLmaxLog + 1].push_back(J);
+        else if (p->opts.band_depth >= 4 && J.K <= (4 << kBandDepthLog)) by_logl[kLmaxLog + 2].push_back(J);
         else wide.push_back(J);
     }
 
@@ -1400,27 +1401,130 @@ cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, i
     return CWT_OK;
 }
 
-// Plan-time tuning (opts.tune = 1): plans with the candidate launch-shape
-// options (the CTA target of the W-writing launches and the intermediate size
-// of a wide-scale launch; a value the caller fixed is kept) are created and
-// timed on this device, running the transform with power on a zero signal
-// into temporary buffers of the output's size (the kernels' work does not
-// depend on the values); the fastest plan is kept and the others destroyed.
+// Plan-time tuning (opts.tune = 1).  Plans with candidate plan options are
+// created and timed on this device, running the transform with power on a zero
+// signal into temporary buffers of the output's size (the kernels' work does
+// not depend on the values); the fastest plan is kept and the others
+// destroyed.  Two stages, each keeping any value the caller fixed:
+//   1. launch shape: the CTA target of the W-writing launches (152, 304, 608)
+//      and the intermediate of a wide-scale launch (16, 32 MiB; 64, 128,
+//      256 MiB with a reduced precision);
+//   2. stage fusion: the band kernels' direct depth (4, 2, 1), i.e. whether a
+//      band of up to 4096 / 2048 bins is evaluated in one pass with the first
+//      DFT stage fed by a Horner sum, or goes through the two-pass path.
+// With the environment variable CWT_TUNE_CACHE naming a file, the choice is
+// looked up there first (keyed by the device and every input of the plan) and
+// appended after tuning, so a later process skips the timing.
+namespace {
+
+constexpr uint64_t kTuneVersion = 2;
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+    const unsigned char* b = (const unsigned char*)data;
+    for (size_t i = 0; i < n; i++) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string tune_key(int64_t N, const double* scales, int32_t n_scales, int32_t wavelet, int32_t boundary,
+                     const cwt_plan_opts& o, std::string* device_name) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    uint64_t h = 14695981039346656037ull;
+    h = fnv1a(h, &kTuneVersion, sizeof(kTuneVersion));
+    h = fnv1a(h, prop.name, std::strlen(prop.name));
+    h = fnv1a(h, &prop.multiProcessorCount, sizeof(int));
+    h = fnv1a(h, &N, sizeof(N));
+    h = fnv1a(h, &n_scales, sizeof(n_scales));
+    h = fnv1a(h, scales, sizeof(double) * (size_t)n_scales);
+    h = fnv1a(h, &wavelet, sizeof(wavelet));
+    h = fnv1a(h, &boundary, sizeof(boundary));
+    const double d[3] = {o.omega0, o.dx, o.eps_trunc};
+    const int64_t q[8] = {o.scale_unit, o.input_dtype, o.fft_len, o.precision, o.min_ctas, o.wide_batch_bytes,
+                          o.band_depth, 0};
+    h = fnv1a(h, d, sizeof(d));
+    h = fnv1a(h, q, sizeof(q));
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+    if (device_name) {
+        *device_name = prop.name;
+        for (char& ch : *device_name)
+            if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+    }
+    return buf;
+}
+
+std::mutex g_tune_mu;
+
+bool tune_cache_lookup(const std::string& key, cwt_plan_opts* o) {
+    const char* path = std::getenv("CWT_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char k[64];
+        int ctas = 0, depth = 0;
+        long long wb = 0;
+        if (std::sscanf(line, "%63s %d %lld %d", k, &ctas, &wb, &depth) == 4 && key == k && ctas > 0 && wb > 0 &&
+            (depth == 1 || depth == 2 || depth == 4)) {
+            o->min_ctas = ctas;
+            o->wide_batch_bytes = wb;
+            o->band_depth = depth;
+            found = true;          // the last entry for a key wins
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string& key, const cwt_plan_opts& o, float ms, const std::string& dev) {
+    const char* path = std::getenv("CWT_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %lld %d %.4f %s\n", key.c_str(), o.min_ctas, (long long)o.wide_batch_bytes, o.band_depth,
+                 ms, dev.c_str());
+    std::fclose(f);
+}
+
+}  // namespace
+
 cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
                         int32_t boundary, const cwt_plan_opts& o) {
-    struct Cand { int32_t ctas; int64_t wb; };
+    std::string dev_name;
+    const std::string key = tune_key(N, scales, n_scales, wavelet, boundary, o, &dev_name);
+    {
+        cwt_plan_opts oc = o;
+        if (tune_cache_lookup(key, &oc)) {
+            oc.tune = 0;
+            cwt_status st = cwt_plan_create_ex(plan, N, scales, n_scales, wavelet, boundary, &oc);
+            if (st == CWT_OK) (*plan)->opts.tune = 1;
+            return st;
+        }
+    }
+    struct Cand { int32_t ctas; int64_t wb; int32_t depth; };
     std::vector<Cand> cands;
     const std::vector<int64_t> wb_cands =
         o.precision == CWT_PRECISION_FP32 ? std::vector<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
                                           : std::vector<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20};
+    const int32_t depth0 = o.band_depth ? o.band_depth : 4;
     for (int32_t c : {152 * 2, 152, 152 * 4})
         for (int64_t wb : wb_cands) {
-            const Cand k{o.min_ctas ? o.min_ctas : c, o.wide_batch_bytes ? o.wide_batch_bytes : wb};
+            const Cand k{o.min_ctas ? o.min_ctas : c, o.wide_batch_bytes ? o.wide_batch_bytes : wb, depth0};
             bool dup = false;
             for (const Cand& q : cands) dup |= q.ctas == k.ctas && q.wb == k.wb;
             if (!dup) cands.push_back(k);
         }
     cwt_plan* best = nullptr;
+    Cand best_c{};
     float best_ms = 0.f;
     void* sig = nullptr;
     void* W = nullptr;
@@ -1434,13 +1538,15 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
         rc = e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : CWT_ERR_CUDA;
         return false;
     };
-    for (const Cand& c : cands) {
+    // creates and times one candidate; keeps it if it is the fastest so far
+    auto try_cand = [&](const Cand& c) -> bool {
         cwt_plan_opts oc = o;
         oc.tune = 0;
         oc.min_ctas = c.ctas;
         oc.wide_batch_bytes = c.wb;
+        oc.band_depth = c.depth;
         cwt_plan* q = nullptr;
-        if ((rc = cwt_plan_create_ex(&q, N, scales, n_scales, wavelet, boundary, &oc)) != CWT_OK) break;
+        if ((rc = cwt_plan_create_ex(&q, N, scales, n_scales, wavelet, boundary, &oc)) != CWT_OK) return false;
         if (!sig) {
             const size_t se = o.input_dtype == CWT_INPUT_F64 ? sizeof(double) : sizeof(float);
             const size_t we = wavelet == CWT_WAVELET_MORLET ? sizeof(float2) : sizeof(float);
@@ -1450,7 +1556,7 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
                 !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) || !cuda_ok(cudaEventCreate(&e0)) ||
                 !cuda_ok(cudaEventCreate(&e1))) {
                 free_plan(q);
-                break;
+                return false;
             }
         }
         float ms = 0.f;
@@ -1462,16 +1568,26 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
         }
         if (rc != CWT_OK) {
             free_plan(q);
-            break;
+            return false;
         }
         if (!best || ms < best_ms) {
             if (best) free_plan(best);
             best = q;
+            best_c = c;
             best_ms = ms;
         } else {
             free_plan(q);
         }
-    }
+        return true;
+    };
+    bool ok = true;
+    for (const Cand& c : cands)
+        if (!(ok = try_cand(c))) break;
+    if (ok && o.band_depth == 0)
+        for (int32_t d : {2, 1}) {
+            const Cand c{best_c.ctas, best_c.wb, d};
+            if (!(ok = try_cand(c))) break;
+        }
     if (st) cudaStreamSynchronize(st);
     if (sig) cudaFree(sig);
     if (W) cudaFree(W);
@@ -1484,6 +1600,7 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
         return rc;
     }
     best->opts.tune = 1;
+    tune_cache_store(key, best->opts, best_ms / 5.f, dev_name);
     *plan = best;
     return CWT_OK;
 }
@@ -1504,7 +1621,7 @@ void cwt_plan_opts_default(cwt_plan_opts* o) {
     o->tune = 0;
     o->wide_batch_bytes = 0;
     o->precision = CWT_PRECISION_FP32;
-    o->pad_ = 0;
+    o->band_depth = 0;
 }
 
 cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
@@ -1534,10 +1651,12 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         if (!std::isfinite(scales[i]) || !(scales[i] > 0.0)) return CWT_ERR_INVALID_ARG;
     if (o.min_ctas < 0 || o.min_ctas > (1 << 20) || o.wide_batch_bytes < 0 ||
         o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1) ||
-        o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3)
+        o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3 ||
+        (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4))
         return CWT_ERR_INVALID_ARG;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;
+    if (o.band_depth == 0) o.band_depth = 4;
     if (o.wide_batch_bytes == 0)
         o.wide_batch_bytes = (int64_t)(o.precision == CWT_PRECISION_FP32 ? kWideBatchBytes : kWideBatchBytesTc);
 

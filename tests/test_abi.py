@@ -74,6 +74,8 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=1 << 26, scales=[2.0], boundary="zero"), 2),          # M > 2^25
     (dict(N=64, scales=[2.0], min_ctas=-1), 1),
     (dict(N=64, scales=[2.0], wide_batch_bytes=-5), 1),
+    (dict(N=64, scales=[2.0], band_depth=3), 1),
+    (dict(N=64, scales=[2.0], band_depth=8), 1),
 ])
 def test_plan_argument_checks(cwt, kwargs, status):
     kw = dict(kwargs)
@@ -119,7 +121,7 @@ def test_plan_options_struct_matches_the_header(cwt):
     assert ctypes.sizeof(o) == 64
     assert (o.omega0, o.dx, o.scale_unit, o.input_dtype, o.fft_len) == (6.0, 1.0, 0, 0, 0)
     assert (o.eps_trunc, o.min_ctas, o.tune, o.wide_batch_bytes) == (1e-10, 0, 0, 0)
-    assert (o.precision, o.pad_) == (0, 0)
+    assert (o.precision, o.band_depth) == (0, 0)
     with open(os.path.join(ROOT, "include", "cwt.h")) as fh:
         text = fh.read()
     body = text[text.index("typedef struct {", text.index("cwt_input_dtype;")):text.index("} cwt_plan_opts;")]

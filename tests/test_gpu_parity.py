@@ -437,8 +437,12 @@ def test_tuned_plan_equals_default(env, boundary):
     p1 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, tune=True)
     o0, o1 = cwt.cwt_plan_get_opts(p0), cwt.cwt_plan_get_opts(p1)
     assert o0["tune"] == 0 and o0["min_ctas"] == 304 and o0["wide_batch_bytes"] == 32 << 20
+    assert o0["band_depth"] == 4
     assert o1["tune"] == 1 and o1["min_ctas"] in (152, 304, 608)
-    assert o1["wide_batch_bytes"] in (16 << 20, 32 << 20)
+    assert o1["wide_batch_bytes"] in (16 << 20, 32 << 20) and o1["band_depth"] in (1, 2, 4)
+    if o1["band_depth"] != 4:       # the tuner fused fewer bands: compare with that stage plan
+        p0.close()
+        p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, band_depth=o1["band_depth"])
     W0, s0 = cwt.cwt_exec_with_power(p0, sig)
     W1, s1 = cwt.cwt_exec_with_power(p1, sig)
     torch.cuda.synchronize()
@@ -446,10 +450,57 @@ def test_tuned_plan_equals_default(env, boundary):
     assert torch.allclose(s0, s1, rtol=1e-5, atol=0)
     # every launch shape gives the same W
     for mc, wb in [(152, 16 << 20), (608, 32 << 20), (1, 1 << 20)]:
-        p2 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, min_ctas=mc, wide_batch_bytes=wb)
+        p2 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, min_ctas=mc, wide_batch_bytes=wb,
+                                 band_depth=cwt.cwt_plan_get_opts(p0)["band_depth"])
         W2 = cwt.cwt_exec(p2, sig)
         torch.cuda.synchronize()
         assert torch.equal(W0, W2), (mc, wb)
         p2.close()
     p0.close()
     p1.close()
+
+
+@pytest.mark.parametrize("depth", [1, 2, 4])
+@pytest.mark.parametrize("wavelet", ["gdw", "morlet"])
+def test_band_depth_variants(env, depth, wavelet):
+    """Stage fusion (band_depth): bands of 1024..4096 bins in one pass with a
+    Horner-fed first stage (depth 2, 4) or through the two-pass path (depth 1);
+    each matches the oracle."""
+    _, _, orc = env
+    N = 1 << 17
+    f = synth.lognormal_field(N, seed=31)
+    sc = synth.log_scales(40.0 if wavelet == "morlet" else 25.0, 800.0, 12)    # bands ~8000 .. 400 bins
+    W, spec, M = run_gpu(env, f, sc, wavelet, "periodic", band_depth=depth)
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=N)
+    assert rel_l2(W, ref) <= TOL
+    P = orc.wavelet_power(ref)
+    assert np.max(np.abs(spec - P) / P) < 1e-4
+
+
+def test_tune_cache_file(env, tmp_path, monkeypatch):
+    """With CWT_TUNE_CACHE set, a tuned plan appends its choice; the next plan
+    of the same inputs reads it instead of timing again."""
+    torch, cwt, _ = env
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("CWT_TUNE_CACHE", str(path))
+    N = 1 << 16
+    sc = synth.log_scales(4.0, N / 4, 20)
+    p1 = cwt.cwt_plan_create(N, sc, "morlet", "zero", tune=True)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    key, ctas, wb, depth, ms, dev = lines[0].split()[:6]
+    o1 = cwt.cwt_plan_get_opts(p1)
+    assert (int(ctas), int(wb), int(depth)) == (o1["min_ctas"], o1["wide_batch_bytes"], o1["band_depth"])
+    assert float(ms) > 0
+    p2 = cwt.cwt_plan_create(N, sc, "morlet", "zero", tune=True)
+    assert path.read_text().splitlines() == lines                   # a cache hit: nothing appended
+    o2 = cwt.cwt_plan_get_opts(p2)
+    assert o2 == o1
+    p3 = cwt.cwt_plan_create(N, sc[:-1], "morlet", "zero", tune=True)   # other inputs: a new entry
+    assert len(path.read_text().splitlines()) == 2
+    sig = torch.tensor(synth.lognormal_field(N, seed=3), dtype=torch.float32, device="cuda")
+    W1, W2 = cwt.cwt_exec(p1, sig), cwt.cwt_exec(p2, sig)
+    torch.cuda.synchronize()
+    assert torch.equal(W1, W2)
+    for p in (p1, p2, p3):
+        p.close()
