@@ -72,6 +72,8 @@ def parse_args():
                     help="tensor-core forms of the 1024-point DFT stages timed beside FP32 (comma list; "
                          "empty: none)")
     # narrower cases of a workload for profiler captures (not a bench line)
+    ap.add_argument("--wide2-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 pass 2 of the wide scales: 1 tile pipeline, 2 CTA Stockham kernel, 0 library default")
     ap.add_argument("--boundary", default="both", choices=["both", "periodic", "zero"],
                     help="run one boundary of the workload only")
     ap.add_argument("--scale-range", type=int, nargs=2, metavar=("I", "J"),
@@ -596,7 +598,8 @@ def run_ours(args):
             w = synth.WORKLOADS[part]
             bounds, sc, sub = workload_subset(args, part)
             for b in bounds:
-                p = cwt.cwt_plan_create(N, sc, w["wavelet"], b, tune=not args.no_tune, precision=precision)
+                p = cwt.cwt_plan_create(N, sc, w["wavelet"], b, tune=not args.no_tune, precision=precision,
+                                        wide2_kernel=args.wide2_kernel)
                 out.append((part, w["wavelet"], b, sc, p, p.empty_output(dev),
                             torch.empty(len(sc), dtype=torch.float64, device=dev)))
         return out, sub
@@ -608,7 +611,7 @@ def run_ours(args):
     fft_lens = [p.M for p in plans]
     transforms = [f"{r[1]}/{r[2]}" for r in runs]
     boundaries_used = sorted({r[2] for r in runs})
-    shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes", "band_depth")}
+    shapes = [{k: cwt.cwt_plan_get_opts(p)[k] for k in ("tune", "min_ctas", "wide_batch_bytes", "band_depth", "wide2_kernel")}
               for p in plans]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 

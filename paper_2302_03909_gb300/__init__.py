@@ -53,7 +53,8 @@ class _Opts(ctypes.Structure):
                 ("fft_len", ctypes.c_int64), ("eps_trunc", ctypes.c_double),
                 ("min_ctas", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("wide_batch_bytes", ctypes.c_int64), ("precision", ctypes.c_int32),
-                ("band_depth", ctypes.c_int32)]
+                ("band_depth", ctypes.c_int32), ("wide2_kernel", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 class CwtError(RuntimeError):
@@ -194,7 +195,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
                     omega0: float = 6.0, dx: float = 1.0, scale_unit: str = "dilation",
                     input_dtype: str = "f32", fft_len: int = 0, eps_trunc: float = 1e-10,
                     min_ctas: int = 0, tune: bool = False, wide_batch_bytes: int = 0,
-                    precision: str = "fp32", band_depth: int = 0) -> Plan:
+                    precision: str = "fp32", band_depth: int = 0, wide2_kernel: int = 0) -> Plan:
     lib = load_library()
     sc = np.ascontiguousarray(scales, dtype=np.float64)
     opts = _Opts()
@@ -209,6 +210,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     opts.wide_batch_bytes = int(wide_batch_bytes)
     opts.precision = PRECISIONS[precision]
     opts.band_depth = int(band_depth)
+    opts.wide2_kernel = int(wide2_kernel)
     h = ctypes.c_void_p()
     st = lib.cwt_plan_create_ex(ctypes.byref(h), int(N),
                                 sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sc),

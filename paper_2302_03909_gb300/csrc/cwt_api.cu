@@ -32,8 +32,8 @@ constexpr int kMaxLogM = 25;           // M <= 2^25 (zero boundary of N = 2^24)
 constexpr int kBandMaxLog = 10;        // band kernels up to L = 1024 when M > kLmax
 constexpr int kWideLog = 10;           // pass-2 DFT length of wide scales (M <= 2^23)
 constexpr size_t kWideBatchBytes = size_t(32) << 20;   // intermediate per wide launch; one per stream
-// the tensor-core pass 2 (reduced precision) pays a fill and drain per launch:
-// larger launches (more tiles per CTA) by default
+// the tile pipeline of pass 2 pays a fill and drain per launch: larger launches
+// (more tiles per CTA) by default
 constexpr size_t kWideBatchBytesTc = size_t(128) << 20;
 
 // ----------------------------------------------------------- launch shapes
@@ -527,9 +527,12 @@ void scale_band(const cwt_plan* p, double wt, double u_lo, double u_hi, int64_t*
 
 size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_stride(T) * sizeof(float2); }
 
-// Pass 2 of the wide scales: the FP32 CUDA-core kernel, or with a reduced
-// precision (opts.precision) and L = 1024 the tensor-core kernel (cwt_tc.cuh)
-bool wide2_on_tc(const cwt_plan* p) { return p->opts.precision != CWT_PRECISION_FP32 && p->wide_logl == 10; }
+// Pass 2 of the wide scales: with L = 1024 the tile pipeline of cwt_tc.cuh
+// (tensor-core stages with a reduced precision, FP32 register stages unless
+// opts.wide2_kernel = 2), else the CTA Stockham kernel
+bool wide2_on_tc(const cwt_plan* p) {
+    return p->wide_logl == 10 && (p->opts.precision != CWT_PRECISION_FP32 || p->opts.wide2_kernel != 2);
+}
 const Entry& wide2_entry(const cwt_plan* p) { return tables().wide2[p->wide_logl][p->crop]; }
 
 cwt_status opt_in_smem(cwt_plan* p, const void* fn);
@@ -1069,7 +1072,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         Q.A = (int32_t)(p->M >> p->wide_logl);
         Q.Y = p->d_Y + (size_t)si * p->y_stride;
         const bool tc = wide2_on_tc(p);
-        Q.yperm = tc ? 1 : 0;                    // Y rows in the tensor-core pass 2's order
+        Q.yperm = tc && p->opts.precision != CWT_PRECISION_FP32;   // Y rows in the tensor-core stages' order
         if (wb.logl1 < 0) {
             const Entry& e1 = tb.wide1[p->wide_loga];
             if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T, wb.count), stage_smem(p->wide_loga, e1.T), Q, ws,
@@ -1102,11 +1105,11 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             Q.err = p->d_err;
             if (!te.fn || !te.gfn) return fail(p, CWT_ERR_INTERNAL, "missing tensor-core pass-2 instantiation");
             if (p->rec) {
-                rec_launch(p, (const void*)te.gfn, grid2, dim3(kTcThreads), tc_smem_bytes(p->opts.precision), ws, Q);
+                rec_launch(p, (const void*)te.gfn, grid2, dim3(kTcThreads), te.gsmem, ws, Q);
             } else {
                 if ((st = opt_in_smem(p, (const void*)te.fn)) != CWT_OK) return st;
                 LaunchTimer lt(p, CWT_KCLASS_WIDE2, wb.out_bytes, ws);
-                te.fn<<<grid2, te.NT, tma_smem_bytes(p->opts.precision), ws>>>(Q, p->ymap);
+                te.fn<<<grid2, te.NT, te.smem, ws>>>(Q, p->ymap);
                 CWT_CUDA(p, cudaGetLastError());
                 lt.done();
             }
@@ -1407,8 +1410,8 @@ cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, i
 // not depend on the values); the fastest plan is kept and the others
 // destroyed.  Two stages, each keeping any value the caller fixed:
 //   1. launch shape: the CTA target of the W-writing launches (152, 304, 608)
-//      and the intermediate of a wide-scale launch (16, 32 MiB; 64, 128,
-//      256 MiB with a reduced precision);
+//      and the intermediate of a wide-scale launch (64, 128, 256 MiB for the
+//      tile pipeline of pass 2; 16, 32 MiB for the CTA Stockham kernel);
 //   2. stage fusion: the band kernels' direct depth (4, 2, 1), i.e. whether a
 //      band of up to 4096 / 2048 bins is evaluated in one pass with the first
 //      DFT stage fed by a Horner sum, or goes through the two-pass path.
@@ -1445,7 +1448,7 @@ std::string tune_key(int64_t N, const double* scales, int32_t n_scales, int32_t 
     h = fnv1a(h, &boundary, sizeof(boundary));
     const double d[3] = {o.omega0, o.dx, o.eps_trunc};
     const int64_t q[8] = {o.scale_unit, o.input_dtype, o.fft_len, o.precision, o.min_ctas, o.wide_batch_bytes,
-                          o.band_depth, 0};
+                          o.band_depth, o.wide2_kernel};
     h = fnv1a(h, d, sizeof(d));
     h = fnv1a(h, q, sizeof(q));
     char buf[32];
@@ -1513,7 +1516,8 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
     struct Cand { int32_t ctas; int64_t wb; int32_t depth; };
     std::vector<Cand> cands;
     const std::vector<int64_t> wb_cands =
-        o.precision == CWT_PRECISION_FP32 ? std::vector<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
+        o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 2
+            ? std::vector<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
                                           : std::vector<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20};
     const int32_t depth0 = o.band_depth ? o.band_depth : 4;
     for (int32_t c : {152 * 2, 152, 152 * 4})
@@ -1622,6 +1626,8 @@ void cwt_plan_opts_default(cwt_plan_opts* o) {
     o->wide_batch_bytes = 0;
     o->precision = CWT_PRECISION_FP32;
     o->band_depth = 0;
+    o->wide2_kernel = 0;
+    o->reserved_ = 0;
 }
 
 cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
@@ -1652,13 +1658,16 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     if (o.min_ctas < 0 || o.min_ctas > (1 << 20) || o.wide_batch_bytes < 0 ||
         o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1) ||
         o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3 ||
-        (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4))
+        (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4) ||
+        o.wide2_kernel < 0 || o.wide2_kernel > 2 || o.reserved_ != 0)
         return CWT_ERR_INVALID_ARG;
+    if (o.wide2_kernel == 0) o.wide2_kernel = 1;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;
     if (o.band_depth == 0) o.band_depth = 4;
     if (o.wide_batch_bytes == 0)
-        o.wide_batch_bytes = (int64_t)(o.precision == CWT_PRECISION_FP32 ? kWideBatchBytes : kWideBatchBytesTc);
+        o.wide_batch_bytes =
+            (int64_t)(o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 2 ? kWideBatchBytes : kWideBatchBytesTc);
 
     int64_t M;
     if (boundary == CWT_BOUNDARY_PERIODIC) {

@@ -39,7 +39,7 @@ struct EntryP { KernFnP fn; KernFnG gfn; int T, NT, logl; };
 // tensor-core pass 2: fn takes the TMA map of the plan's Y and runs NT threads
 // (plain launches); gfn is the grouped form (kTcThreads threads, cp.async)
 using KernFnTma = void (*)(Params, CUtensorMap);
-struct TcEntry { KernFnTma fn; KernFnG gfn; int NT; };
+struct TcEntry { KernFnTma fn; KernFnG gfn; int NT; size_t smem, gsmem; };   // gfn: kTcThreads threads
 
 template <int LOGL, int T, bool CROP, int RD = 1>
 Entry band_entry() { return {k_band<LOGL, T, CROP, RD>, k_band_g<LOGL, T, CROP, RD>, T, T * col_threads(LOGL), LOGL}; }
@@ -63,7 +63,7 @@ struct Tables {
     Entry wide2[kLmaxLog + 1][2];           // [log2 L][crop]
     Entry fwd2[kLmaxLog + 1];
     EntryP wide1p[kLmaxLog + 1][kP1Var];    // [log2 L1][column-count variant]
-    TcEntry wide2_tc[5][2];                 // pass 2 with L = 1024 on the tensor cores: [precision][crop]
+    TcEntry wide2_tc[5][2];                 // pass 2 with L = 1024, tile pipeline: [precision][crop]
 };
 
 void fill_band_tables(Tables& t);   // cwt_tab_band.cu

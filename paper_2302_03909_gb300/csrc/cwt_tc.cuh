@@ -376,13 +376,14 @@ __device__ __forceinline__ void tc_nt_range(const Params& p, bool crop, int d0, 
     nt1 = (int)(chi < 0 ? 0 : (chi / 256 + 1 < 4 ? chi / 256 + 1 : 4));
 }
 
-// W rows from a staging tile (rows i = tc_rho(c) for outputs c): thread k of
+// W rows from a staging tile (rows i = tc_rho(c) for outputs c; i = c with
+// RHO = false, the FP32 tile pipeline's natural order): thread k of
 // NTHR (a multiple of 128) stores columns 2 (k & 3), + 1 of the rows
 // i = r0 + R m, r0 = k >> 2, R = NTHR / 4, m < 4096 / NTHR.  tc_rho permutes
 // bits, so c = tc_rho(r0) + tc_rho(R m) and the slot of row i is the slot of
 // r0 plus 8 R m: every address is a per-thread base plus a constant.
 // Accumulates |W|^2 into pw0 (Morlet, GDW row a) and pw1 (GDW row b).
-template <int NTHR, bool CROP>
+template <int NTHR, bool CROP, bool RHO = true>
 __device__ __forceinline__ void tc_store_tile(const float2* buf, const Params& p, const Job& J, int d0, int k,
                                               float& pw0, float& pw1) {
     constexpr int R = NTHR / 4, NM = 1024 / R, B = 8;   // rows per thread, loads in flight
@@ -391,7 +392,7 @@ __device__ __forceinline__ void tc_store_tile(const float2* buf, const Params& p
     const unsigned len = (unsigned)p.out_len;
     const int wc = k & 3, r0 = k >> 2;
     const float2* src = buf + tc_slot(r0, 2 * wc);
-    const int c0 = tc_rho(r0);
+    const int c0 = RHO ? tc_rho(r0) : r0;
     const int n0 = d0 + 2 * wc + A * c0;          // output index of row r0's first column
     if (!wav_real(p.wavelet)) {
         float2* row = (float2*)p.W + (int64_t)J.g[0].row * p.out_len + (n0 - off);
@@ -403,7 +404,7 @@ __device__ __forceinline__ void tc_store_tile(const float2* buf, const Params& p
             for (int b = 0; b < B; b++) v[b] = *reinterpret_cast<const float4*>(src + 8 * R * (m0 + b));
 #pragma unroll
             for (int b = 0; b < B; b++) {
-                const int dc = tc_rho(R * (m0 + b));
+                const int dc = RHO ? tc_rho(R * (m0 + b)) : R * (m0 + b);
                 float2* q2 = row + (int64_t)A * dc;
                 bool k0 = true, k1 = true;
                 if (CROP) {
@@ -432,7 +433,7 @@ __device__ __forceinline__ void tc_store_tile(const float2* buf, const Params& p
             for (int b = 0; b < B; b++) v[b] = *reinterpret_cast<const float4*>(src + 8 * R * (m0 + b));
 #pragma unroll
             for (int b = 0; b < B; b++) {
-                const int dc = tc_rho(R * (m0 + b));
+                const int dc = RHO ? tc_rho(R * (m0 + b)) : R * (m0 + b);
                 bool k0 = true, k1 = true;
                 if (CROP) {
                     const int n = n0 + A * dc;

@@ -205,11 +205,12 @@ def _pow2(x: int) -> int:
 def _plan_bound(M: int, S: int) -> int:
     """Upper bound on the device workspace of one plan of transform length M
     with S rows: the spectrum (M/2 + 1 complex64) and its transposed copy (M),
-    the wide-scale intermediate (three streams, each max(M, 4 Mi) complex64),
+    the wide-scale intermediate (three streams, each max(M, 16 Mi) complex64,
+    the default 128 MiB batch of wide scales per launch),
     the band values (at most 4096 complex64 per row), the power partial sums
     (fewer than M / 256 per row), the edge tables of a zero-boundary plan
     (2 x 4096 + 1 complex64 per row) and 2 MiB of small tables."""
-    return 16 * M + 3 * max(8 * M, 32 << 20) + S * (96 << 10) + S * (M // 32) + (2 << 20)
+    return 16 * M + 3 * max(8 * M, 128 << 20) + S * (96 << 10) + S * (M // 32) + (2 << 20)
 
 
 def workspace_bound(N: int, scales, wavelet: str, boundary: str) -> int:

@@ -76,6 +76,8 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=64, scales=[2.0], wide_batch_bytes=-5), 1),
     (dict(N=64, scales=[2.0], band_depth=3), 1),
     (dict(N=64, scales=[2.0], band_depth=8), 1),
+    (dict(N=64, scales=[2.0], wide2_kernel=3), 1),
+    (dict(N=64, scales=[2.0], wide2_kernel=-1), 1),
 ])
 def test_plan_argument_checks(cwt, kwargs, status):
     kw = dict(kwargs)
@@ -118,10 +120,10 @@ def test_plan_options_struct_matches_the_header(cwt):
     the defaults the library fills in."""
     o = cwt._Opts()
     cwt.load_library().cwt_plan_opts_default(ctypes.byref(o))
-    assert ctypes.sizeof(o) == 64
+    assert ctypes.sizeof(o) == 72
     assert (o.omega0, o.dx, o.scale_unit, o.input_dtype, o.fft_len) == (6.0, 1.0, 0, 0, 0)
     assert (o.eps_trunc, o.min_ctas, o.tune, o.wide_batch_bytes) == (1e-10, 0, 0, 0)
-    assert (o.precision, o.band_depth) == (0, 0)
+    assert (o.precision, o.band_depth, o.wide2_kernel, o.reserved_) == (0, 0, 0, 0)
     with open(os.path.join(ROOT, "include", "cwt.h")) as fh:
         text = fh.read()
     body = text[text.index("typedef struct {", text.index("cwt_input_dtype;")):text.index("} cwt_plan_opts;")]

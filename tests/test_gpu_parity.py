@@ -457,10 +457,10 @@ def test_tuned_plan_equals_default(env, boundary):
     p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary)
     p1 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, tune=True)
     o0, o1 = cwt.cwt_plan_get_opts(p0), cwt.cwt_plan_get_opts(p1)
-    assert o0["tune"] == 0 and o0["min_ctas"] == 304 and o0["wide_batch_bytes"] == 32 << 20
-    assert o0["band_depth"] == 4
+    assert o0["tune"] == 0 and o0["min_ctas"] == 304 and o0["wide_batch_bytes"] == 128 << 20
+    assert o0["band_depth"] == 4 and o0["wide2_kernel"] == 1
     assert o1["tune"] == 1 and o1["min_ctas"] in (152, 304, 608)
-    assert o1["wide_batch_bytes"] in (16 << 20, 32 << 20) and o1["band_depth"] in (1, 2, 4)
+    assert o1["wide_batch_bytes"] in (64 << 20, 128 << 20, 256 << 20) and o1["band_depth"] in (1, 2, 4)
     if o1["band_depth"] != 4:       # the tuner fused fewer bands: compare with that stage plan
         p0.close()
         p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, band_depth=o1["band_depth"])
@@ -496,6 +496,37 @@ def test_band_depth_variants(env, depth, wavelet):
     assert rel_l2(W, ref) <= TOL
     P = orc.wavelet_power(ref)
     assert np.max(np.abs(spec - P) / P) < 1e-4
+
+
+@pytest.mark.parametrize("wavelet", ["gdw", "morlet"])
+@pytest.mark.parametrize("boundary", ["periodic", "zero"])
+def test_wide2_kernels_agree(env, wavelet, boundary):
+    """The two FP32 forms of the wide scales' pass 2 (the tile pipeline and the
+    CTA Stockham kernel) run the same radix-32 x 32 arithmetic on the same
+    tables: W is bit-equal between them, the power spectra agree to rounding,
+    and the tile pipeline matches the oracle over the whole array."""
+    torch, cwt, orc = env
+    N = 1 << 18
+    f = synth.lognormal_field(N, seed=47)
+    sc = synth.log_scales(2.0, 400.0, 16)           # bands of ~280000 .. 1400 bins: wide and band scales
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    out = {}
+    for k in (1, 2):
+        plan = cwt.cwt_plan_create(N, sc, wavelet, boundary, wide2_kernel=k)
+        assert cwt.cwt_plan_get_opts(plan)["wide2_kernel"] == k
+        cwt.cwt_plan_set_timing(plan, 1)
+        W, spec = cwt.cwt_exec_with_power(plan, sig)
+        torch.cuda.synchronize()
+        assert cwt.cwt_plan_get_timing(plan)["wide2"][1] > 0      # pass 2 ran
+        out[k] = (W, spec.cpu().numpy(), plan.M)
+        plan.close()
+    assert torch.equal(out[1][0], out[2][0])
+    assert np.max(np.abs(out[1][1] - out[2][1]) / out[2][1]) < 1e-5
+    W = out[1][0].cpu().numpy().astype(np.complex128)
+    ref = orc.cwt_fft(f32(f), sc, wavelet, M=out[1][2])
+    assert rel_l2(W, ref) <= TOL
+    P = orc.wavelet_power(ref)
+    assert np.max(np.abs(out[1][1] - P) / P) < 1e-4
 
 
 def test_tune_cache_file(env, tmp_path, monkeypatch):
