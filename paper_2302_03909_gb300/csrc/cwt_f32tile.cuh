@@ -64,9 +64,11 @@ __device__ __forceinline__ void f32_build_twiddles(const float2* __restrict__ tw
 // group's warp u takes column 4 g + ((u + l / 8) mod 4).  With
 // B = tc_slot(l, c), row 32 u + (l ^ v) of column c lies at slot
 // 256 u + (B ^ K(v)), K(v) = 8 v + 2 ((v >> 1) & 3), and row l + 32 u at
-// slot 256 u + B.  The two groups synchronise independently, so one group's
-// shared-memory phases overlap the other's arithmetic.
-__device__ __forceinline__ void f32_tile_dft(float2* buf, const float2* __restrict__ twf, int bar) {
+// slot 256 u + B.  The two groups synchronise independently, and group 1
+// enters its first tile only when group 0 has written its exchange (named
+// barrier 7, once), so that one group's shared-memory phases overlap the
+// other's arithmetic.
+__device__ __forceinline__ void f32_tile_dft(float2* buf, const float2* __restrict__ twf, int bar, bool lead) {
     const int t = threadIdx.x, l = t & 31, g = t >> 7;
     const int c = 4 * g + ((((t >> 5) & 3) + (l >> 3)) & 3);
     const int B = tc_slot(l, c);
@@ -81,6 +83,7 @@ __device__ __forceinline__ void f32_tile_dft(float2* buf, const float2* __restri
 #pragma unroll
     for (int c1 = 0; c1 < 32; c1++) buf[256 * c1 + (B ^ (8 * c1 + 2 * ((c1 >> 1) & 3)))] = v[c1];
     named_sync(bar, 128);
+    if (lead && g == 0) named_arrive(7, 256);    // releases group 1 into its first tile
 #pragma unroll
     for (int b0 = 0; b0 < 32; b0++) v[b0] = buf[256 * l + (B ^ (8 * b0 + 2 * ((b0 >> 1) & 3)))];
     named_sync(bar, 128);                        // the exchange is read before the outputs overwrite it
@@ -125,7 +128,8 @@ __device__ __forceinline__ void wide2_f32_body(const Params& p, const CUtensorMa
 #pragma unroll 1
         for (int q = 0; q < ntile; q++) {
             if (!mbar_wait(&full[q % NB], (q / NB) & 1)) ok = false;
-            f32_tile_dft(bufs + (q % NB) * kTcTile, twf, 5);
+            if (q == 0 && tid >= 128) named_sync(7, 256);   // group 1 starts half a tile behind group 0
+            f32_tile_dft(bufs + (q % NB) * kTcTile, twf, 5, q == 0);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // in-place writes before later copies
             named_arrive(1 + q % 3, NT);         // tile q's outputs are in its buffer
         }
@@ -195,7 +199,8 @@ __device__ __forceinline__ void wide2_f32_g_body(const Params& p, const Cta c) {
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
-        f32_tile_dft(buf, twf, 5);
+        if (q == 0 && tid >= 128) named_sync(7, 256);
+        f32_tile_dft(buf, twf, 5, q == 0);
         __syncthreads();
         if (tid < kF32Store) tc_store_tile<kF32Store, CROP, false>(buf, p, J, d0, tid, pw0, pw1);
     }
