@@ -445,6 +445,8 @@ def run_serving(args, embedded=False):
         torch.cuda.synchronize()
         out[label] = serving.run_trace(srv, [dataclasses_replace(r) for r in trace])
         srv.close()
+        del srv
+        torch.cuda.empty_cache()
     mean_units = float(np.mean([len(r.scales) * r.N for r in trace]))
     line = {"impl": "ours", "metric": "CWT serving latency", "unit": "ms", "higher_is_better": False,
             "p50_ms": out["concurrent"]["p50_ms"], "p99_ms": out["concurrent"]["p99_ms"],
@@ -772,6 +774,7 @@ def run_ours(args):
                  "signals": b["config"]["signals"], "scale_samples": b["config"]["scale_samples"],
                  "grouped_info": b["detail"]["grouped_info"], "what": b["config"]["timed"]}
     if rank == 0 and world == 1 and not args.no_serving:
+        torch.cuda.empty_cache()
         sv = run_serving(args, embedded=True)
         serving_line = {k: sv[k] for k in ("p50_ms", "p99_ms", "serial_p50_ms", "serial_p99_ms",
                                            "offered_scale_samples_per_s")}

@@ -320,7 +320,17 @@ class Server:
     def _make_plan(self, key):
         torch = self.torch
         N, scales, wavelet, boundary = key
-        p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary)
+        try:
+            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary)
+        except self.cwt.CwtError as e:
+            # device memory that torch's caching allocator holds (freed request
+            # buffers) is not visible to the library's allocations: release it
+            # and try once more
+            if e.status != 3:
+                raise
+            torch.cuda.synchronize(self.dev)
+            torch.cuda.empty_cache()
+            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary)
         p._io, p._io_bytes = None, 0
         if self._owns_buffers(Request(-1, *key, 0.0)):
             p._io = (torch.empty(N, dtype=torch.float32, device=self.dev), p.empty_output(self.dev),

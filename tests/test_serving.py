@@ -172,3 +172,53 @@ def test_workspace_bound_grows_with_the_transform():
     assert b(1 << 12, sc, "morlet", "zero") > b(1 << 12, sc, "morlet", "periodic")
     assert b(5000, sc, "gdw", "periodic") > b(4096, sc, "gdw", "periodic")
     assert b(1 << 20, sc * 2, "gdw", "zero") > b(1 << 20, sc, "gdw", "zero")
+
+
+def test_plan_creation_retries_once_after_releasing_the_torch_cache():
+    """A plan that fails with CWT_ERR_OOM is created again after the torch
+    caching allocator has released its free blocks; any other error, or a
+    second OOM, propagates."""
+    import paper_2302_03909_gb300 as cwt
+
+    calls = {"create": 0, "empty": 0}
+
+    class FakeCuda:
+        @staticmethod
+        def synchronize(dev=None):
+            pass
+
+        @staticmethod
+        def empty_cache():
+            calls["empty"] += 1
+
+    class FakeTorch:
+        cuda = FakeCuda
+
+    def make_cwt(fail_times, status=3):
+        class FakeCwt:
+            CwtError = cwt.CwtError
+
+            @staticmethod
+            def cwt_plan_create(N, scales, wavelet, boundary):
+                calls["create"] += 1
+                if calls["create"] <= fail_times:
+                    raise cwt.CwtError(status, "out of memory")
+                return FakePlan((N, tuple(scales), wavelet, boundary), 1000)
+        return FakeCwt
+
+    srv = serving.Server.__new__(serving.Server)
+    srv.torch, srv.dev, srv.reuse = FakeTorch, None, False
+    key = (1024, (2.0, 4.0), "gdw", "periodic")
+    srv.cwt = make_cwt(1)
+    p = srv._make_plan(key)
+    assert p.workspace_bytes == 1000 and calls == {"create": 2, "empty": 1}
+    calls.update(create=0, empty=0)
+    srv.cwt = make_cwt(2)
+    with pytest.raises(cwt.CwtError):
+        srv._make_plan(key)
+    assert calls == {"create": 2, "empty": 1}
+    calls.update(create=0, empty=0)
+    srv.cwt = make_cwt(1, status=1)
+    with pytest.raises(cwt.CwtError):
+        srv._make_plan(key)
+    assert calls == {"create": 1, "empty": 0}
