@@ -213,8 +213,11 @@ cwt_status cwt_icwt(cwt_plan* plan, const void* W_dev, float* f_out_dev, void* s
 
 /* Host-buffer form of cwt_exec_with_power: copies the signal from host memory,
  * runs the transform in plan-owned device buffers (allocated on first use) and
- * copies W and, if spectrum_host is not NULL, the spectrum back.  Pinned host
- * memory gives the fastest copies.  Returns after the results are on the host. */
+ * copies W and, if spectrum_host is not NULL, the spectrum back.  Each group of
+ * W rows is copied as soon as the launch that finishes it is done, on a
+ * plan-owned second stream, so the copies overlap the rest of the transform.
+ * Pinned host memory gives the fastest copies (pageable memory works but does
+ * not overlap).  Returns after the results are on the host. */
 cwt_status cwt_exec_host(cwt_plan* plan, const void* signal_host, void* W_host,
                          double* spectrum_host, void* stream);
 

@@ -458,6 +458,8 @@ void free_plan(cwt_plan* p) {
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_pre) cudaEventDestroy(p->ev_pre);
     if (p->ev_pfwd) cudaEventDestroy(p->ev_pfwd);
+    for (cudaEvent_t e : p->hc_ev) cudaEventDestroy(e);
+    if (p->hc_stream) cudaStreamDestroy(p->hc_stream);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
@@ -621,6 +623,8 @@ cwt_status build_plan(cwt_plan* p) {
         g.ntiles = 0;
         g.tj_off = tile_job.size();
         g.bytes = 0;
+        g.job0 = (int)p->jobs.size();
+        g.njobs = (int)by_logl[slot].size();
         for (Job J : by_logl[slot]) {
             J.tile0 = g.ntiles;
             int idx = (int)p->jobs.size();
@@ -912,6 +916,41 @@ cwt_status check_device(cwt_plan* p) {
     return CWT_OK;
 }
 
+// W rows of jobs j0 .. j0 + n - 1
+std::vector<int> rows_of_jobs(const cwt_plan* p, int j0, int n) {
+    std::vector<int> r;
+    for (int j = j0; j < j0 + n; j++)
+        for (int q = 0; q < 2; q++)
+            if (p->jobs[j].g[q].row >= 0) r.push_back(p->jobs[j].g[q].row);
+    return r;
+}
+
+// cwt_exec_host: the W rows `rows` are final once the work queued on `s` so
+// far is done.  The copy stream waits for that point and copies them to the
+// host (runs of consecutive rows as one copy) while later launches run.
+cwt_status host_copy_rows(cwt_plan* p, cudaStream_t s, std::vector<int> rows) {
+    auto& h = p->hc;
+    if (!h.on || rows.empty()) return CWT_OK;
+    if (h.nev == p->hc_ev.size()) {
+        cudaEvent_t e = nullptr;
+        CWT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->hc_ev.push_back(e);
+    }
+    cudaEvent_t e = p->hc_ev[h.nev++];
+    CWT_CUDA(p, cudaEventRecord(e, s));
+    CWT_CUDA(p, cudaStreamWaitEvent(p->hc_stream, e, 0));
+    std::sort(rows.begin(), rows.end());
+    for (size_t i = 0; i < rows.size();) {
+        size_t j = i + 1;
+        while (j < rows.size() && rows[j] == rows[j - 1] + 1) j++;
+        const size_t off = (size_t)rows[i] * h.row_bytes, n = (j - i) * h.row_bytes;
+        CWT_CUDA(p, cudaMemcpyAsync(h.dst + off, h.src + off, n, cudaMemcpyDeviceToHost, p->hc_stream));
+        for (size_t k = i; k < j; k++) h.done[rows[k]] = 1;
+        i = j;
+    }
+    return CWT_OK;
+}
+
 cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     const Tables& tb = tables();
     cwt_status st;
@@ -1058,7 +1097,12 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
             if ((st = ev_wait(p, streams[i], p->ev_fork)) != CWT_OK) return st;
         }
     }
-    if (p->child && (st = edge_fix(streams[nstreams - 1])) != CWT_OK) return st;
+    if (p->child) {
+        if ((st = edge_fix(streams[nstreams - 1])) != CWT_OK) return st;
+        std::vector<int> cr(p->child_n);
+        for (int i = 0; i < p->child_n; i++) cr[i] = p->child_r0 + i;
+        if ((st = host_copy_rows(p, streams[nstreams - 1], cr)) != CWT_OK) return st;
+    }
     int next = 0;
     // wide batches first (longest chains), round robin; band groups fill in
     for (size_t wi = 0; wi < p->wide.size(); wi++) {
@@ -1117,6 +1161,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
                                 wb.out_bytes)) != CWT_OK) {
             return st;
         }
+        if ((st = host_copy_rows(p, ws, rows_of_jobs(p, wb.job0, wb.count))) != CWT_OK) return st;
     }
     for (size_t gi = 0; gi < p->groups.size(); gi++) {
         const auto& g = p->groups[gi];
@@ -1128,6 +1173,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         size_t smem = (size_t)((1 << g.rdi) << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
         cudaStream_t gs = streams[next++ % nstreams];
         if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
+        if ((st = host_copy_rows(p, gs, rows_of_jobs(p, g.job0, g.njobs))) != CWT_OK) return st;
     }
     for (int i = 1; i < nstreams; i++) {
         if ((st = ev_record(p, p->ev_join[i - 1], streams[i])) != CWT_OK) return st;
@@ -1170,7 +1216,7 @@ bool take_timeout(cwt_plan* p) {
 cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     if (take_timeout(p)) return fail(p, CWT_ERR_TIMEOUT, "a tensor-core pass 2 of an earlier call gave up waiting");
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (p->timing || !p->graphs_ok || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread ||
+    if (p->timing || p->hc.on || !p->graphs_ok || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread ||
         cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return run_launches(p, signal, W, spectrum, s);
     if (p->gexec && p->gkey[0] == signal && p->gkey[1] == W && p->gkey[2] == spectrum) {
@@ -1826,10 +1872,46 @@ cwt_status cwt_exec_host(cwt_plan* plan, const void* signal_host, void* W_host, 
     if (!plan->h_W) CWT_CUDA(plan, cudaMalloc(&plan->h_W, w_bytes));
     if (!plan->h_spec) CWT_CUDA(plan, cudaMalloc((void**)&plan->h_spec, (size_t)plan->S * sizeof(double)));
     cudaStream_t s = (cudaStream_t)stream;
+    if (!plan->hc_stream) CWT_CUDA(plan, cudaStreamCreateWithFlags(&plan->hc_stream, cudaStreamNonBlocking));
+    if (plan->hc_ev.empty()) {                   // [0]: joins the copy stream back into s
+        cudaEvent_t e = nullptr;
+        CWT_CUDA(plan, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        plan->hc_ev.push_back(e);
+    }
     CWT_CUDA(plan, cudaMemcpyAsync(plan->h_sig, signal_host, sig_bytes, cudaMemcpyHostToDevice, s));
+    // rows of W are copied out as the launches that finish them complete
+    // (host_copy_rows), overlapping the copy with the rest of the transform
+    auto& h = plan->hc;
+    h.on = true;
+    h.dst = (char*)W_host;
+    h.src = (const char*)plan->h_W;
+    h.row_bytes = (size_t)plan->N * we;
+    h.done.assign((size_t)plan->S, 0);
+    h.nev = 1;
     st = run(plan, plan->h_sig, plan->h_W, spectrum_host ? plan->h_spec : nullptr, s);
-    if (st != CWT_OK) return st;
-    CWT_CUDA(plan, cudaMemcpyAsync(W_host, plan->h_W, w_bytes, cudaMemcpyDeviceToHost, s));
+    h.on = false;
+    if (h.nev > 1) {
+        CWT_CUDA(plan, cudaEventRecord(plan->hc_ev[0], plan->hc_stream));
+        CWT_CUDA(plan, cudaStreamWaitEvent(s, plan->hc_ev[0], 0));
+    }
+    if (st != CWT_OK) {
+        cudaStreamSynchronize(s);
+        return st;
+    }
+    // rows no launch reported (sub-plans, a plan whose rows all come from its
+    // child): copied after the whole transform, runs of rows at a time
+    for (int32_t r = 0; r < plan->S;) {
+        if (h.done[r]) {
+            r++;
+            continue;
+        }
+        int32_t e = r + 1;
+        while (e < plan->S && !h.done[e]) e++;
+        CWT_CUDA(plan, cudaMemcpyAsync((char*)W_host + (size_t)r * h.row_bytes, (const char*)plan->h_W +
+                                       (size_t)r * h.row_bytes, (size_t)(e - r) * h.row_bytes,
+                                       cudaMemcpyDeviceToHost, s));
+        r = e;
+    }
     if (spectrum_host)
         CWT_CUDA(plan, cudaMemcpyAsync(spectrum_host, plan->h_spec, (size_t)plan->S * sizeof(double),
                                        cudaMemcpyDeviceToHost, s));

@@ -61,7 +61,7 @@ struct cwt_plan {
     std::vector<double> w_tilde;
 
     std::vector<cwtk::Job> jobs;
-    struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; };  // depth 2^rdi
+    struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; int job0, njobs; };  // depth 2^rdi
     std::vector<BandGroup> groups;        // single-pass jobs by DFT length
     struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
@@ -90,6 +90,19 @@ struct cwt_plan {
     void* h_sig = nullptr;
     void* h_W = nullptr;
     double* h_spec = nullptr;
+    // cwt_exec_host: rows of W go to the host as soon as the launch that
+    // finishes them is done, on a copy stream that waits for that launch
+    // (set only during that call; rows it does not reach are copied at the end)
+    struct HostCopy {
+        bool on = false;
+        char* dst = nullptr;              // host W
+        const char* src = nullptr;        // device W of this call
+        size_t row_bytes = 0;
+        std::vector<char> done;           // per row: copy issued
+        size_t nev = 0;                   // events used in this call
+    } hc;
+    cudaStream_t hc_stream = nullptr;
+    std::vector<cudaEvent_t> hc_ev;
     // cwt_wavelet_power scratch
     double* d_pw_partials = nullptr;
     int64_t pw_chunks = 0;

@@ -153,6 +153,36 @@ def test_standalone_power_and_host_path(env):
     plan.close()
 
 
+@pytest.mark.parametrize("N,wavelet,boundary,smin,smax,S", [
+    (1 << 18, "morlet", "zero", 2.0, 4000.0, 24),       # child rows, band groups, wide batches
+    (1 << 18, "gdw", "periodic", 2.0, 4000.0, 24),
+    (1 << 15, "gdw", "zero", 2.0, 4.0, 4),              # every row from the child plan
+    (100003, "morlet", "periodic", 4.0, 2000.0, 12),    # sub-plans (N not a power of two)
+])
+def test_host_path_overlapped_copies(env, N, wavelet, boundary, smin, smax, S):
+    """cwt_exec_host copies each group of W rows to the host as soon as the
+    launch that finishes it is done, on a second stream: W and the power
+    spectrum equal the device path's bit for bit, on two calls into different
+    pinned buffers (no stale destination), for plans with a child plan, band
+    groups and wide batches, every row from the child, and sub-plans."""
+    torch, cwt, _ = env
+    f = synth.lognormal_field(N, seed=61)
+    sc = synth.log_scales(smin, smax, S)
+    plan = cwt.cwt_plan_create(N, sc, wavelet, boundary)
+    sig = torch.tensor(f, dtype=torch.float32, device="cuda")
+    W, spec = cwt.cwt_exec_with_power(plan, sig)
+    torch.cuda.synchronize()
+    Wd, sd = W.cpu(), spec.cpu()
+    sig_h = torch.tensor(f, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        Wh = torch.full(tuple(W.shape), float("nan"), dtype=W.dtype).pin_memory()
+        sh = torch.full((S,), float("nan"), dtype=torch.float64).pin_memory()
+        cwt.cwt_exec_host(plan, sig_h, Wh, sh)
+        assert torch.equal(Wh, Wd)
+        assert torch.equal(sh, sd)
+    plan.close()
+
+
 def test_repeatable_bitwise(env):
     torch, cwt, _ = env
     N = 1 << 16
