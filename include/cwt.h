@@ -122,7 +122,8 @@ typedef struct {
     int32_t min_ctas;    /* launch shape: the W-writing launches take up to 8 tiles per CTA while
                             keeping at least this many CTAs (0: 304, two per SM; at most 2^20) */
     int32_t tune;        /* 1: at creation, time plans with min_ctas in {152, 304, 608} and
-                            wide_batch_bytes in {64, 128, 256} MiB ({16, 32} MiB with
+                            wide_batch_bytes in {32, 128, 256} MiB ({64, 128, 256} with
+                            wide2_kernel = 1 or a reduced precision, {16, 32} with
                             wide2_kernel = 2), then band_depth in {4, 2, 1} (a nonzero value given for any of
                             them is kept) on this device and keep the fastest.  Needs temporary device
                             memory of the output's size and runs the transform a few times.  If the
@@ -130,7 +131,7 @@ typedef struct {
                             the same device and plan inputs is used without timing, and new choices are
                             appended to it (one line each).  0: no tuning */
     int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
-                            (0: 128 MiB, 32 MiB with wide2_kernel = 2; at most 2^36) */
+                            (0: 128 MiB, 32 MiB with the Stockham pass 2; at most 2^36) */
     int32_t precision;   /* cwt_precision of the 1024-point DFT stages (default CWT_PRECISION_FP32) */
     int32_t band_depth;  /* stage fusion: bands of up to band_depth * 1024 bins (1, 2 or 4) are computed in
                             one pass, the band kernel's first DFT stage filled by a Horner sum of band_depth
@@ -139,7 +140,8 @@ typedef struct {
                             1: the tile pipeline (tiles of 8 columns copied by TMA, one warp per
                             column with two register radix-32 stages, separate store warps);
                             2: the CTA Stockham kernel (one column per 32 threads, Y read by the
-                            DFT threads).  0: 1.  The reduced precisions always take the tile
+                            DFT threads).  0: chosen per plan, 1 for transform lengths
+                            M >= 2^21, 2 below.  The reduced precisions always take the tile
                             pipeline (tensor-core stages) */
     int32_t reserved_;   /* must be 0 */
 } cwt_plan_opts;

@@ -529,9 +529,10 @@ void scale_band(const cwt_plan* p, double wt, double u_lo, double u_hi, int64_t*
 
 size_t stage_smem(int logl, int T) { return (size_t)(1 << logl) * (size_t)row_stride(T) * sizeof(float2); }
 
-// Pass 2 of the wide scales: with L = 1024 the tile pipeline of cwt_tc.cuh
-// (tensor-core stages with a reduced precision, FP32 register stages unless
-// opts.wide2_kernel = 2), else the CTA Stockham kernel
+// Pass 2 of the wide scales: with L = 1024 the tile pipeline (tensor-core
+// stages of cwt_tc.cuh with a reduced precision; in FP32 the register stages
+// of cwt_f32tile.cuh unless opts.wide2_kernel, resolved per plan, is 2), else
+// the CTA Stockham kernel
 bool wide2_on_tc(const cwt_plan* p) {
     return p->wide_logl == 10 && (p->opts.precision != CWT_PRECISION_FP32 || p->opts.wide2_kernel != 2);
 }
@@ -642,21 +643,14 @@ cwt_status build_plan(cwt_plan* p) {
         const int T2 = tb.wide2[p->wide_logl][0].T;
         p->wide_G = (int)std::max<int64_t>(1, p->opts.wide_batch_bytes / (int64_t)((size_t)M * sizeof(float2)));
         const int64_t tiles_job = (A + T2 - 1) / T2;
-        if (wide2_on_tc(p)) {
-            // the tensor-core pass 2 is resident as one CTA per SM: about one CTA per
-            // SM per launch, each looping over its tiles (set-up paid once, the next
-            // tile's copy in flight during the current tile's work)
-            int sms = 152;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-            const int64_t per = std::max<int64_t>(1, sms / std::min<int64_t>(p->wide_G, (int64_t)wide.size()));
-            p->wide_D = (int)((tiles_job + per - 1) / per);
-        } else {
-            p->wide_D = pick_D(tiles_job * std::min<int64_t>(p->wide_G, (int64_t)wide.size()), p->opts.min_ctas);
-        }
-        const int ntiles2 = (int)((tiles_job + p->wide_D - 1) / p->wide_D);
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
         const int L = 1 << p->wide_logl;
+        // batches: up to wide_G consecutive jobs with the same pass-1 shape
+        const size_t job_base = p->jobs.size();
+        std::vector<int> batch_of(wide.size());
         for (size_t i = 0; i < wide.size(); i++) {
-            Job J = wide[i];
+            const Job& J = wide[i];
             // pass 1 of column b has at most ceil(K / L) band bins: a pruned band tile of
             // L1 = 2^ceil(log2) points over A1 = A / L1 columns d1, with the widest
             // column-count variant that fits A1; the whole A-point DFT when L1 = A, and
@@ -671,13 +665,30 @@ cwt_status build_plan(cwt_plan* p) {
             if (var < 0) l1 = -1;
             if (p->wide.empty() || p->wide.back().count >= p->wide_G || p->wide.back().logl1 != l1 ||
                 p->wide.back().var != var)
-                p->wide.push_back({(int)p->jobs.size(), 0, l1, var, 0.0, 0.0});
-            J.tile0 = 0;
-            assign_parts(J, ntiles2);
+                p->wide.push_back({(int)(job_base + i), 0, l1, var, 0.0, 0.0, 1});
             auto& wb = p->wide.back();
             wb.count++;
             wb.band_bytes += 8.0 * J.K;
             wb.out_bytes += job_rows(J) * out_row_bytes(p);
+            batch_of[i] = (int)p->wide.size() - 1;
+        }
+        // pass-2 tiles per CTA, from each batch's own job count (batches split by
+        // pass-1 shape are often smaller than wide_G).  The tile pipeline is
+        // resident as one CTA per SM: about one CTA per SM per launch, each
+        // looping over its tiles (set-up, fill and drain paid once per CTA).
+        for (auto& wb : p->wide) {
+            if (wide2_on_tc(p)) {
+                const int64_t per = std::max<int64_t>(1, sms / wb.count);
+                wb.D = (int)((tiles_job + per - 1) / per);
+            } else {
+                wb.D = pick_D(tiles_job * wb.count, p->opts.min_ctas);
+            }
+        }
+        for (size_t i = 0; i < wide.size(); i++) {
+            Job J = wide[i];
+            J.tile0 = 0;
+            const int D = p->wide[batch_of[i]].D;
+            assign_parts(J, (int)((tiles_job + D - 1) / D));
             p->jobs.push_back(J);
         }
     }
@@ -1140,7 +1151,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
                 lt.done();
             }
         }
-        Q.D = p->wide_D;
+        Q.D = wb.D;
         const int tiles2 = (Q.A + e2.T - 1) / e2.T;
         const dim3 grid2((tiles2 + Q.D - 1) / Q.D, wb.count);
         if (tc) {
@@ -1466,7 +1477,7 @@ cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, i
 // appended after tuning, so a later process skips the timing.
 namespace {
 
-constexpr uint64_t kTuneVersion = 2;
+constexpr uint64_t kTuneVersion = 3;   // 3: pass-2 kernel chosen per plan, per-batch pass-2 grids
 
 uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
     const unsigned char* b = (const unsigned char*)data;
@@ -1564,6 +1575,8 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
     const std::vector<int64_t> wb_cands =
         o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 2
             ? std::vector<int64_t>{int64_t(32) << 20, int64_t(16) << 20}
+        : o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 0
+            ? std::vector<int64_t>{int64_t(128) << 20, int64_t(32) << 20, int64_t(256) << 20}
                                           : std::vector<int64_t>{int64_t(128) << 20, int64_t(64) << 20, int64_t(256) << 20};
     const int32_t depth0 = o.band_depth ? o.band_depth : 4;
     for (int32_t c : {152 * 2, 152, 152 * 4})
@@ -1707,13 +1720,11 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4) ||
         o.wide2_kernel < 0 || o.wide2_kernel > 2 || o.reserved_ != 0)
         return CWT_ERR_INVALID_ARG;
-    if (o.wide2_kernel == 0) o.wide2_kernel = 1;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;
     if (o.band_depth == 0) o.band_depth = 4;
-    if (o.wide_batch_bytes == 0)
-        o.wide_batch_bytes =
-            (int64_t)(o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 2 ? kWideBatchBytes : kWideBatchBytesTc);
+    const int32_t req_wide2_kernel = o.wide2_kernel;      // as given (0: chosen per plan)
+    const int64_t req_wide_batch_bytes = o.wide_batch_bytes;
 
     int64_t M;
     if (boundary == CWT_BOUNDARY_PERIODIC) {
@@ -1734,6 +1745,13 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         }
     }
     if (M < 2 || M > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
+    // the wide scales' FP32 pass 2: the tile pipeline from M = 2^21, where it
+    // measured faster, the CTA Stockham kernel below; the default wide batch
+    // follows the kernel
+    if (o.wide2_kernel == 0) o.wide2_kernel = M >= (int64_t(1) << 21) ? 1 : 2;
+    if (o.wide_batch_bytes == 0)
+        o.wide_batch_bytes =
+            (int64_t)(o.precision == CWT_PRECISION_FP32 && o.wide2_kernel == 2 ? kWideBatchBytes : kWideBatchBytesTc);
 
     cwt_plan* p = new (std::nothrow) cwt_plan();
     if (!p) return CWT_ERR_OOM;
@@ -1772,6 +1790,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
             cwt_plan_opts co = o;
             co.scale_unit = CWT_SCALE_W_TILDE;
             co.fft_len = 0;
+            co.wide2_kernel = req_wide2_kernel;          // the child chooses by its own length
+            co.wide_batch_bytes = req_wide_batch_bytes;
             cwt_status cs = cwt_plan_create_ex(&p->child, N, p->w_tilde.data() + r0, r1 - r0, wavelet,
                                                CWT_BOUNDARY_PERIODIC, &co);
             if (cs != CWT_OK) {

@@ -63,9 +63,9 @@ struct cwt_plan {
     std::vector<cwtk::Job> jobs;
     struct BandGroup { int logl; int rdi; int ntiles; int D; size_t tj_off; double bytes; int job0, njobs; };  // depth 2^rdi
     std::vector<BandGroup> groups;        // single-pass jobs by DFT length
-    struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; };  // logl1 < 0: full pass 1
+    struct WideBatch { int job0; int count; int logl1, var; double band_bytes, out_bytes; int D; };  // logl1 < 0: full pass 1; D: pass-2 tiles per CTA
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
-    int wide_logl = 0, wide_loga = 0, wide_G = 0, wide_D = 1;
+    int wide_logl = 0, wide_loga = 0, wide_G = 0;
     size_t y_stride = 0;                  // elements of Y per stream
     int fwd_small = 0;
     int crop = 0;                         // N < M: drop the padded outputs

@@ -487,10 +487,14 @@ def test_tuned_plan_equals_default(env, boundary):
     p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary)
     p1 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, tune=True)
     o0, o1 = cwt.cwt_plan_get_opts(p0), cwt.cwt_plan_get_opts(p1)
-    assert o0["tune"] == 0 and o0["min_ctas"] == 304 and o0["wide_batch_bytes"] == 128 << 20
-    assert o0["band_depth"] == 4 and o0["wide2_kernel"] == 1
+    # pass 2: the tile pipeline from M = 2^21 (the zero boundary's M = 2N), the
+    # Stockham kernel with its 32 MiB batches below
+    tile = boundary == "zero"
+    assert o0["tune"] == 0 and o0["min_ctas"] == 304
+    assert o0["wide_batch_bytes"] == (128 << 20 if tile else 32 << 20)
+    assert o0["band_depth"] == 4 and o0["wide2_kernel"] == (1 if tile else 2)
     assert o1["tune"] == 1 and o1["min_ctas"] in (152, 304, 608)
-    assert o1["wide_batch_bytes"] in (64 << 20, 128 << 20, 256 << 20) and o1["band_depth"] in (1, 2, 4)
+    assert o1["wide_batch_bytes"] in (32 << 20, 128 << 20, 256 << 20) and o1["band_depth"] in (1, 2, 4)
     if o1["band_depth"] != 4:       # the tuner fused fewer bands: compare with that stage plan
         p0.close()
         p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, band_depth=o1["band_depth"])

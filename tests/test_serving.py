@@ -199,7 +199,8 @@ def test_plan_creation_retries_once_after_releasing_the_torch_cache():
             CwtError = cwt.CwtError
 
             @staticmethod
-            def cwt_plan_create(N, scales, wavelet, boundary):
+            def cwt_plan_create(N, scales, wavelet, boundary, **opts):
+                assert opts == {"wide2_kernel": 2}
                 calls["create"] += 1
                 if calls["create"] <= fail_times:
                     raise cwt.CwtError(status, "out of memory")
@@ -207,7 +208,7 @@ def test_plan_creation_retries_once_after_releasing_the_torch_cache():
         return FakeCwt
 
     srv = serving.Server.__new__(serving.Server)
-    srv.torch, srv.dev, srv.reuse = FakeTorch, None, False
+    srv.torch, srv.dev, srv.reuse, srv.plan_opts = FakeTorch, None, False, {"wide2_kernel": 2}
     key = (1024, (2.0, 4.0), "gdw", "periodic")
     srv.cwt = make_cwt(1)
     p = srv._make_plan(key)
