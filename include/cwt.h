@@ -124,7 +124,7 @@ typedef struct {
     int32_t tune;        /* 1: at creation, time plans with min_ctas in {152, 304, 608} and
                             wide_batch_bytes in {32, 128, 256} MiB ({64, 128, 256} with
                             wide2_kernel = 1 or a reduced precision, {16, 32} with
-                            wide2_kernel = 2), then band_depth in {4, 2, 1} (a nonzero value given for any of
+                            wide2_kernel = 2), then band_depth in {4, 8, 16, 2, 1} (a nonzero value given for any of
                             them is kept) on this device and keep the fastest.  Needs temporary device
                             memory of the output's size and runs the transform a few times.  If the
                             environment variable CWT_TUNE_CACHE names a file, a choice stored there for
@@ -133,7 +133,7 @@ typedef struct {
     int64_t wide_batch_bytes; /* launch shape: intermediate of one wide-scale launch, one per stream
                             (0: 128 MiB, 32 MiB with the Stockham pass 2; at most 2^36) */
     int32_t precision;   /* cwt_precision of the 1024-point DFT stages (default CWT_PRECISION_FP32) */
-    int32_t band_depth;  /* stage fusion: bands of up to band_depth * 1024 bins (1, 2 or 4) are computed in
+    int32_t band_depth;  /* stage fusion: bands of up to band_depth * 1024 bins (1, 2, 4, 8 or 16) are computed in
                             one pass, the band kernel's first DFT stage filled by a Horner sum of band_depth
                             terms; wider bands take the two-pass path.  0: 4 (or tuned) */
     int32_t wide2_kernel; /* pass 2 of the wide scales (1024-point DFTs over Y's columns) in FP32:

@@ -582,9 +582,9 @@ cwt_status build_plan(cwt_plan* p) {
     const bool small = M <= kLmax;
     p->wide_logl = std::max(kWideLog, p->logM - kLmaxLog);
     p->wide_loga = p->logM - p->wide_logl;
-    // band groups by (log2 L, direct depth): slots kLmaxLog + 1 and + 2 hold the
-    // L = 1024 groups of depth 2 and 4 (bands up to 2048 / 4096 bins)
-    std::vector<std::vector<Job>> by_logl(kLmaxLog + 3);
+    // band groups by (log2 L, direct depth): slots kLmaxLog + 1 .. + 4 hold the
+    // L = 1024 groups of depth 2, 4, 8 and 16 (bands up to 2048 .. 16384 bins)
+    std::vector<std::vector<Job>> by_logl(kLmaxLog + 1 + kBandRdMax);
     std::vector<Job> wide;
     for (const Job& J : all) {
         int lk = std::max(1, ilog2(J.K));
@@ -592,6 +592,8 @@ cwt_status build_plan(cwt_plan* p) {
         else if (lk <= kBandMaxLog) by_logl[lk].push_back(J);
         else if (p->opts.band_depth >= 2 && J.K <= (2 << kBandDepthLog)) by_logl[kLmaxLog + 1].push_back(J);
         else if (p->opts.band_depth >= 4 && J.K <= (4 << kBandDepthLog)) by_logl[kLmaxLog + 2].push_back(J);
+        else if (p->opts.band_depth >= 8 && J.K <= (8 << kBandDepthLog)) by_logl[kLmaxLog + 3].push_back(J);
+        else if (p->opts.band_depth >= 16 && J.K <= (16 << kBandDepthLog)) by_logl[kLmaxLog + 4].push_back(J);
         else wide.push_back(J);
     }
 
@@ -609,7 +611,7 @@ cwt_status build_plan(cwt_plan* p) {
             nparts += ntiles;
         }
     };
-    for (int slot = 1; slot <= kLmaxLog + 2; slot++) {
+    for (int slot = 1; slot <= kLmaxLog + kBandRdMax; slot++) {
         if (by_logl[slot].empty()) continue;
         const int ll = slot <= kLmaxLog ? slot : kBandDepthLog;
         cwt_plan::BandGroup g;
@@ -1647,7 +1649,7 @@ cwt_status create_tuned(cwt_plan** plan, int64_t N, const double* scales, int32_
     for (const Cand& c : cands)
         if (!(ok = try_cand(c))) break;
     if (ok && o.band_depth == 0)
-        for (int32_t d : {2, 1}) {
+        for (int32_t d : {8, 16, 2, 1}) {
             const Cand c{best_c.ctas, best_c.wb, d};
             if (!(ok = try_cand(c))) break;
         }
@@ -1717,7 +1719,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
     if (o.min_ctas < 0 || o.min_ctas > (1 << 20) || o.wide_batch_bytes < 0 ||
         o.wide_batch_bytes > (int64_t(1) << 36) || (o.tune != 0 && o.tune != 1) ||
         o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3 ||
-        (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4) ||
+        (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4 && o.band_depth != 8 &&
+         o.band_depth != 16) ||
         o.wide2_kernel < 0 || o.wide2_kernel > 2 || o.reserved_ != 0)
         return CWT_ERR_INVALID_ARG;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);

@@ -15,6 +15,10 @@ void fill_band_tables(Tables& t) {
     t.band_rd[1][1] = band_entry<kBandDepthLog, band_T(kBandDepthLog), true, 2>();
     t.band_rd[2][0] = band_entry<kBandDepthLog, band_T(kBandDepthLog), false, 4>();
     t.band_rd[2][1] = band_entry<kBandDepthLog, band_T(kBandDepthLog), true, 4>();
+    t.band_rd[3][0] = band_entry<kBandDepthLog, band_T(kBandDepthLog), false, 8>();
+    t.band_rd[3][1] = band_entry<kBandDepthLog, band_T(kBandDepthLog), true, 8>();
+    t.band_rd[4][0] = band_entry<kBandDepthLog, band_T(kBandDepthLog), false, 16>();
+    t.band_rd[4][1] = band_entry<kBandDepthLog, band_T(kBandDepthLog), true, 16>();
 }
 
 }  // namespace cwtk

@@ -27,8 +27,10 @@ constexpr int wide1p_T(int logl) { return band_T(logl); }
 // pruned pass-1 variants: column count T = min(wide1p_T(L1), 128 >> q), q < kP1Var
 constexpr int kP1Var = 7;
 constexpr int p1var_T(int logl, int q) { return wide1p_T(logl) < (128 >> q) ? wide1p_T(logl) : (128 >> q); }
-// direct depths of the L = 1024 band kernel (bands up to RD * 1024 bins)
+// direct depths of the L = 1024 band kernel (bands up to RD * 1024 bins,
+// RD = 2^i for i <= kBandRdMax)
 constexpr int kBandDepthLog = 10;
+constexpr int kBandRdMax = 4;
 
 // fn: the kernel; gfn: its grouped form (one launch over several plans' launches)
 using KernFn = void (*)(Params);
@@ -56,7 +58,7 @@ EntryP wide1p_entry() { return {k_wide1p<LOGL, T>, k_wide1p_g<LOGL, T>, T, T * c
 
 struct Tables {
     Entry band[kLmaxLog + 1][2];            // [log2 L][crop]
-    Entry band_rd[3][2];                    // L = 1024 with direct depth 2^(i): [i][crop], i = 1, 2
+    Entry band_rd[kBandRdMax + 1][2];       // L = 1024 with direct depth 2^(i): [i][crop], i = 1 .. kBandRdMax
     Entry wide1[kLmaxLog + 1];
     Entry fwd1[kLmaxLog + 1];
     Entry fwd_small[kLmaxLog + 1];

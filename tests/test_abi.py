@@ -75,7 +75,7 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=64, scales=[2.0], min_ctas=-1), 1),
     (dict(N=64, scales=[2.0], wide_batch_bytes=-5), 1),
     (dict(N=64, scales=[2.0], band_depth=3), 1),
-    (dict(N=64, scales=[2.0], band_depth=8), 1),
+    (dict(N=64, scales=[2.0], band_depth=32), 1),
     (dict(N=64, scales=[2.0], wide2_kernel=3), 1),
     (dict(N=64, scales=[2.0], wide2_kernel=-1), 1),
 ])

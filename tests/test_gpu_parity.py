@@ -494,7 +494,7 @@ def test_tuned_plan_equals_default(env, boundary):
     assert o0["wide_batch_bytes"] == (128 << 20 if tile else 32 << 20)
     assert o0["band_depth"] == 4 and o0["wide2_kernel"] == (1 if tile else 2)
     assert o1["tune"] == 1 and o1["min_ctas"] in (152, 304, 608)
-    assert o1["wide_batch_bytes"] in (32 << 20, 128 << 20, 256 << 20) and o1["band_depth"] in (1, 2, 4)
+    assert o1["wide_batch_bytes"] in (32 << 20, 128 << 20, 256 << 20) and o1["band_depth"] in (1, 2, 4, 8, 16)
     if o1["band_depth"] != 4:       # the tuner fused fewer bands: compare with that stage plan
         p0.close()
         p0 = cwt.cwt_plan_create(len(f), sc, "morlet", boundary, band_depth=o1["band_depth"])
@@ -515,16 +515,17 @@ def test_tuned_plan_equals_default(env, boundary):
     p1.close()
 
 
-@pytest.mark.parametrize("depth", [1, 2, 4])
+@pytest.mark.parametrize("depth", [1, 2, 4, 8, 16])
 @pytest.mark.parametrize("wavelet", ["gdw", "morlet"])
 def test_band_depth_variants(env, depth, wavelet):
-    """Stage fusion (band_depth): bands of 1024..4096 bins in one pass with a
-    Horner-fed first stage (depth 2, 4) or through the two-pass path (depth 1);
-    each matches the oracle."""
+    """Stage fusion (band_depth): bands of 1024..16384 bins in one pass with a
+    Horner-fed first stage (depth 2 .. 16) or through the two-pass path (depth
+    1); each matches the oracle."""
     _, _, orc = env
     N = 1 << 17
     f = synth.lognormal_field(N, seed=31)
-    sc = synth.log_scales(40.0 if wavelet == "morlet" else 25.0, 800.0, 12)    # bands ~8000 .. 400 bins
+    lo = (40.0 if wavelet == "morlet" else 25.0) / (2.0 if depth == 16 else 1.0)
+    sc = synth.log_scales(lo, 800.0, 12)           # bands ~8000 (~16000 for depth 16) .. 400 bins
     W, spec, M = run_gpu(env, f, sc, wavelet, "periodic", band_depth=depth)
     ref = orc.cwt_fft(f32(f), sc, wavelet, M=N)
     assert rel_l2(W, ref) <= TOL
