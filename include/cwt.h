@@ -68,10 +68,12 @@ typedef enum {
 } cwt_wavelet;
 
 typedef enum {
-    CWT_BOUNDARY_PERIODIC = 0, /* the N-periodic FFTCWT.  N a power of two: M = N.  Otherwise (GDW and
-                                  Morlet only) the same result through zero-padded transforms of the
-                                  periodically extended signal; scales whose spectrum is not negligible
-                                  (1e-7) at the Nyquist frequency give CWT_ERR_UNSUPPORTED */
+    CWT_BOUNDARY_PERIODIC = 0, /* the N-periodic FFTCWT.  N a power of two: M = N.  Otherwise, for
+                                  the GDW and the Morlet, the same result through zero-padded
+                                  transforms of the periodically extended signal; rows where that does
+                                  not apply (the CBSW and CW-GDW, scales whose spectrum is not
+                                  negligible (1e-7) at the Nyquist frequency) through Bluestein's chirp
+                                  transform on power-of-two FFTs of length >= 2N - 1 (at most 2^25) */
     CWT_BOUNDARY_ZERO = 1      /* zero padding to M = next power of two >= 2N (Eq. 40 context).  With
                                   fft_len 0, the same result with less padding where a scale's wavelet
                                   is short: N a power of two, a periodic N-point transform plus an edge

@@ -20,6 +20,7 @@
 #include "../../include/cwt.h"
 #include "cwt_kernels.cuh"
 #include "cwt_tables.cuh"
+#include "cwt_bluestein.cuh"
 #include "cwt_tc.cuh"
 #include "cwt_plan_impl.h"
 
@@ -466,6 +467,9 @@ void free_plan(cwt_plan* p) {
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    void* bsb[] = {p->d_bs_chirp, p->d_bs_G, p->d_bs_work};
+    for (void* q : bsb)
+        if (q) cudaFree(q);
     void* edge[] = {p->d_edge_rows, p->d_edge_h, p->d_edge_delta};
     for (void* q : edge)
         if (q) cudaFree(q);
@@ -499,12 +503,14 @@ double out_row_bytes(const cwt_plan* p) {
 
 double job_rows(const Job& J) { return (J.g[0].row >= 0) + (J.g[1].row >= 0); }
 
-ScaleGen make_gen(const cwt_plan* p, double wt, int row) {
+// the scale's psi_hat generator on the grid of Mg points (0: the plan's M)
+ScaleGen make_gen(const cwt_plan* p, double wt, int row, int64_t Mg = 0) {
     ScaleGen g{};
-    double alpha = 2.0 * kPi / ((double)p->M * wt);
+    const double Mgrid = (double)(Mg ? Mg : p->M);
+    double alpha = 2.0 * kPi / (Mgrid * wt);
     g.a_hi = (float)alpha;
     g.a_lo = (float)(alpha - (double)g.a_hi);
-    g.amp = (float)(std::sqrt(p->opts.dx / wt) / (double)p->M *
+    g.amp = (float)(std::sqrt(p->opts.dx / wt) / Mgrid *
                     wavelet_spectrum_const(p->wavelet, p->opts.omega0));
     double k0 = p->opts.omega0 / alpha;
     double k0i = std::floor(k0);
@@ -539,6 +545,32 @@ bool wide2_on_tc(const cwt_plan* p) {
 const Entry& wide2_entry(const cwt_plan* p) { return tables().wide2[p->wide_logl][p->crop]; }
 
 cwt_status opt_in_smem(cwt_plan* p, const void* fn);
+
+// twiddle tables of length p->M (FP64 generated, FP32 stored): the two-level
+// e^{-2 pi i j / M} and the stage tables e^{-2 pi i i / L}, L <= kLmax
+cwt_status upload_twiddles(cwt_plan* p) {
+    const int64_t M = p->M;
+    p->h = (p->logM + 1) / 2;
+    std::vector<float2> lo(size_t(1) << p->h), hi(size_t(1) << (p->logM - p->h)), tt(2 * kLmax);
+    for (size_t j = 0; j < lo.size(); j++) {
+        double a = -2.0 * kPi * (double)j / (double)M;
+        lo[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    for (size_t j = 0; j < hi.size(); j++) {
+        double a = -2.0 * kPi * (double)(j << p->h) / (double)M;
+        hi[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    tt[0] = tt[1] = make_float2(1.f, 0.f);
+    for (int L = 2; L <= kLmax; L *= 2)
+        for (int i = 0; i < L; i++) {
+            double a = -2.0 * kPi * (double)i / (double)L;
+            tt[L + i] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    cwt_status st;
+    if ((st = upload(p, &p->d_tw_lo, lo)) != CWT_OK) return st;
+    if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
+    return upload(p, &p->d_tw_tab, tt);
+}
 
 cwt_status build_plan(cwt_plan* p) {
     const Tables& tb = tables();
@@ -700,32 +732,12 @@ cwt_status build_plan(cwt_plan* p) {
     p->fwd_in_bytes = (double)p->N * (p->opts.input_dtype == CWT_INPUT_F64 ? 8.0 : 4.0);
     p->fwd_out_bytes = 8.0 * (double)(M / 2 + 1);
 
-    // twiddle tables (FP64 generated, FP32 stored)
-    p->h = (p->logM + 1) / 2;
-    std::vector<float2> lo(size_t(1) << p->h), hi(size_t(1) << (p->logM - p->h)), tt(2 * kLmax);
-    for (size_t j = 0; j < lo.size(); j++) {
-        double a = -2.0 * kPi * (double)j / (double)M;
-        lo[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    for (size_t j = 0; j < hi.size(); j++) {
-        double a = -2.0 * kPi * (double)(j << p->h) / (double)M;
-        hi[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    tt[0] = tt[1] = make_float2(1.f, 0.f);
-    for (int L = 2; L <= kLmax; L *= 2)
-        for (int i = 0; i < L; i++) {
-            double a = -2.0 * kPi * (double)i / (double)L;
-            tt[L + i] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-
     cwt_status st;
     if ((st = upload(p, &p->d_jobs, p->jobs)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_tile_job, tile_job)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_part_off, p->part_off)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_part_cnt, p->part_cnt)) != CWT_OK) return st;
-    if ((st = upload(p, &p->d_tw_lo, lo)) != CWT_OK) return st;
-    if ((st = upload(p, &p->d_tw_hi, hi)) != CWT_OK) return st;
-    if ((st = upload(p, &p->d_tw_tab, tt)) != CWT_OK) return st;
+    if ((st = upload_twiddles(p)) != CWT_OK) return st;
     if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
     if (!p->wide.empty() && (st = dev_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
     size_t ycount = 0;
@@ -929,6 +941,31 @@ cwt_status check_device(cwt_plan* p) {
     return CWT_OK;
 }
 
+// The forward kernels over M = p->M points: one CTA when M <= kLmax, else the
+// A-point column DFTs (pass 1, through p->d_Y) and the L-point DFTs (pass 2).
+// P selects the input (the real signal, or P.cin) and the output (P.Fp_out, by
+// P.cmode).
+cwt_status launch_forward(cwt_plan* p, const Params& P, cudaStream_t fs, double in_bytes, double out_bytes) {
+    const Tables& tb = tables();
+    cwt_status st;
+    if (p->fwd_small) {
+        const Entry& e = tb.fwd_small[p->logM];
+        Params Q = P;
+        Q.A = 1;
+        return launch(p, e, dim3(1), stage_smem(p->logM, 1), Q, fs, CWT_KCLASS_FORWARD, in_bytes + out_bytes);
+    }
+    const Entry& e1 = tb.fwd1[p->wide_loga];
+    const int L = 1 << p->wide_logl;
+    if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga, e1.T), P, fs, CWT_KCLASS_FORWARD,
+                     in_bytes)) != CWT_OK)
+        return st;
+    const Entry& e2 = tb.fwd2[p->wide_logl];
+    Params Q = P;
+    Q.A = (int32_t)(p->M >> p->wide_logl);
+    return launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, fs, CWT_KCLASS_FORWARD,
+                  out_bytes);
+}
+
 // W rows of jobs j0 .. j0 + n - 1
 std::vector<int> rows_of_jobs(const cwt_plan* p, int j0, int n) {
     std::vector<int> r;
@@ -964,8 +1001,87 @@ cwt_status host_copy_rows(cwt_plan* p, cudaStream_t s, std::vector<int> rows) {
     return CWT_OK;
 }
 
+// Periodic boundary for any N (a plan made by create_bluestein): the chirp
+// transform of cwt_bluestein.cuh on the call's stream.  Signal stage:
+// X = f c, X2 = conj(D(X) D(conj c)), Cv = conj(D(X2)) = P conv1.  Per job:
+// X = psi-product Cv / P, X2 = conj(D(X) D(c)), X = conj(D(X2)), W = conj(c) X / P.
+cwt_status run_bluestein(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
+    using BsFn = void (*)(BsArgs);
+    const int64_t P = p->M;
+    float2* X = p->d_bs_work;
+    float2* X2 = X + P;
+    float2* Cv = X + 2 * P;
+    const Params B = base_params(p);
+    BsArgs a{};
+    a.signal = signal;
+    a.chirp = p->d_bs_chirp;
+    a.W = W;
+    a.partials = p->d_partials;
+    a.N = p->N;
+    a.P = (int32_t)P;
+    a.sig_f64 = B.sig_f64;
+    a.wavelet = p->wavelet;
+    a.do_power = spectrum != nullptr;
+    a.half_w0sq = B.half_w0sq;
+    a.corr_v2 = B.corr_v2;
+    a.inv_p = (float)(1.0 / (double)P);
+    const unsigned gp = (unsigned)std::min<int64_t>((P + kBsThreads - 1) / kBsThreads, 4096);
+    const unsigned go = (unsigned)((p->N + kBsOutBlock - 1) / kBsOutBlock);
+    auto elem = [&](BsFn fn, const void* gfn, unsigned grid, int cls, double bytes) -> cwt_status {
+        if (p->rec) {
+            rec_launch(p, gfn, dim3(grid), dim3(kBsThreads), 0, s, a);
+            return CWT_OK;
+        }
+        LaunchTimer lt(p, cls, bytes, s);
+        fn<<<grid, kBsThreads, 0, s>>>(a);
+        CWT_CUDA(p, cudaGetLastError());
+        lt.done();
+        return CWT_OK;
+    };
+    auto fft = [&](const float2* in, float2* out, const float2* G, int mode) -> cwt_status {
+        Params Q = B;
+        Q.cin = in;
+        Q.Fp_out = out;
+        Q.cG = G;
+        Q.cmode = mode;
+        Q.Y = p->d_Y;
+        return launch_forward(p, Q, s, 8.0 * (double)P, 8.0 * (double)P);
+    };
+    cwt_status st;
+    a.dst = X;
+    if ((st = elem(k_bs_sig, (const void*)k_bs_sig_g, gp, CWT_KCLASS_FORWARD, 4.0 * (double)p->N)) != CWT_OK) return st;
+    if ((st = fft(X, X2, p->d_bs_G, 1)) != CWT_OK) return st;
+    if ((st = fft(X2, Cv, nullptr, 2)) != CWT_OK) return st;
+    for (const Job& J : p->jobs) {
+        a.J = J;
+        a.src = Cv;
+        a.dst = X;
+        if ((st = elem(k_bs_scale, (const void*)k_bs_scale_g, gp, CWT_KCLASS_WIDE1, 0.0)) != CWT_OK) return st;
+        if ((st = fft(X, X2, p->d_bs_G + P, 1)) != CWT_OK) return st;
+        if ((st = fft(X2, X, nullptr, 2)) != CWT_OK) return st;
+        a.src = X;
+        if ((st = elem(k_bs_out, (const void*)k_bs_out_g, go, CWT_KCLASS_WIDE2, job_rows(J) * out_row_bytes(p))) !=
+            CWT_OK)
+            return st;
+    }
+    if (spectrum) {
+        LaunchTimer lt(p, CWT_KCLASS_POWER, 8.0 * (double)(p->n_partials + p->S), s);
+        if (p->rec) {
+            const PowerArgs pa{p->d_partials, p->d_part_off, p->d_part_cnt, spectrum, p->out_len, p->S, 0};
+            rec_launch(p, (const void*)k_power_finalize_g, dim3(p->S), dim3(32), 0, s, pa);
+        } else {
+            k_power_finalize<<<p->S, 32, 0, s>>>(p->d_partials, p->d_part_off, p->d_part_cnt, p->S, p->out_len,
+                                                 spectrum);
+            CWT_CUDA(p, cudaGetLastError());
+            lt.done();
+        }
+    }
+    return CWT_OK;
+}
+
 cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     const Tables& tb = tables();
+    if (p->bs) return run_bluestein(p, signal, W, spectrum, s);
     cwt_status st;
     if (!p->subs.empty()) {                      // N not a power of two: sub-plans by padded length
         const int f64 = p->opts.input_dtype == CWT_INPUT_F64;
@@ -1052,26 +1168,7 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
     }
 
     // 1. forward transform F(m) = sum_n f(n) e^{+2 pi i m n / M}, m <= M/2
-    if (p->fwd_small) {
-        const Entry& e = tb.fwd_small[p->logM];
-        Params Q = P;
-        Q.A = 1;
-        if ((st = launch(p, e, dim3(1), stage_smem(p->logM, 1), Q, fs, CWT_KCLASS_FORWARD,
-                         p->fwd_in_bytes + p->fwd_out_bytes)) != CWT_OK)
-            return st;
-    } else {
-        const Entry& e1 = tb.fwd1[p->wide_loga];
-        const int L = 1 << p->wide_logl;
-        if ((st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga, e1.T), P, fs,
-                         CWT_KCLASS_FORWARD, p->fwd_in_bytes)) != CWT_OK)
-            return st;
-        const Entry& e2 = tb.fwd2[p->wide_logl];
-        Params Q = P;
-        Q.A = (int32_t)(p->M >> p->wide_logl);
-        if ((st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, fs,
-                         CWT_KCLASS_FORWARD, p->fwd_out_bytes)) != CWT_OK)
-            return st;
-    }
+    if ((st = launch_forward(p, P, fs, p->fwd_in_bytes, p->fwd_out_bytes)) != CWT_OK) return st;
 
     // the wide scales' pass 1 reads the spectrum column by column: transpose it once
     if (!p->wide.empty()) {
@@ -1284,22 +1381,134 @@ cwt_status plan_check_device(cwt_plan* p) { return check_device(p); }
 // length M >= N + 3E form one zero-boundary sub-plan of fft_len M.  Scales
 // whose spectrum is not negligible (1e-7 of its peak) at the Nyquist frequency
 // are refused: their band-limited wavelet rings instead of decaying.
+// Periodic boundary for any N, every wavelet and every scale: the N-point
+// transforms of Eqs. 8-9 by Bluestein's chirp transform (cwt_bluestein.cuh)
+// over power-of-two FFTs of length P >= 2N - 1.  wt: the rows' w~.  No band
+// truncation: every bin of the N-point grid enters.
+cwt_status create_bluestein(cwt_plan** plan, int64_t N, const double* wt, int32_t n_scales, int32_t wavelet,
+                            const cwt_plan_opts& o) {
+    int64_t P = 4;
+    while (P < 2 * N - 1) P <<= 1;
+    if (P > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
+    cwt_plan* p = new (std::nothrow) cwt_plan();
+    if (!p) return CWT_ERR_OOM;
+    p->N = N;
+    p->out_len = N;
+    p->M = P;
+    p->logM = ilog2(P);
+    p->S = n_scales;
+    p->wavelet = wavelet;
+    p->boundary = CWT_BOUNDARY_PERIODIC;
+    p->opts = o;
+    p->opts.scale_unit = CWT_SCALE_W_TILDE;
+    p->w_tilde.assign(wt, wt + n_scales);
+    p->bs = true;
+    p->fwd_small = P <= kLmax;
+    p->wide_logl = std::max(kWideLog, p->logM - kLmaxLog);
+    p->wide_loga = p->logM - p->wide_logl;
+    auto bail = [&](cwt_status st) {
+        free_plan(p);
+        return st;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(CWT_ERR_CUDA);
+    // jobs: a Morlet row each, or two real-wavelet rows; one power partial per
+    // output block of each row
+    const int per = wav_real(wavelet) ? 2 : 1;
+    const int64_t nb = (N + kBsOutBlock - 1) / kBsOutBlock;
+    p->part_off.assign(n_scales, 0);
+    p->part_cnt.assign(n_scales, 0);
+    int64_t nparts = 0;
+    for (int32_t i0 = 0; i0 < n_scales; i0 += per) {
+        Job J{};
+        for (int q = 0; q < 2; q++) {
+            const int32_t s = i0 + q;
+            if (q < per && s < n_scales) {
+                J.g[q] = make_gen(p, wt[s], s, N);
+                J.g[q].part_off = (int32_t)nparts;
+                p->part_off[s] = (int32_t)nparts;
+                p->part_cnt[s] = (int32_t)nb;
+                nparts += nb;
+            } else {
+                J.g[q] = ScaleGen{};
+                J.g[q].row = -1;
+            }
+        }
+        J.k_lo = 0;
+        J.K = (int32_t)N;
+        p->jobs.push_back(J);
+    }
+    p->n_partials = nparts;
+    // c_j = e^{i pi j^2 / N}, the phase reduced exactly: j^2 mod 2N
+    std::vector<float2> chirp((size_t)N);
+    for (int64_t j = 0; j < N; j++) {
+        const int64_t r = (int64_t)(((unsigned __int128)j * (unsigned __int128)j) % (unsigned __int128)(2 * N));
+        const double ang = kPi * (double)r / (double)N;
+        chirp[(size_t)j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    cwt_status st;
+    if ((st = upload(p, &p->d_jobs, p->jobs)) != CWT_OK) return bail(st);
+    if ((st = upload(p, &p->d_part_off, p->part_off)) != CWT_OK) return bail(st);
+    if ((st = upload(p, &p->d_part_cnt, p->part_cnt)) != CWT_OK) return bail(st);
+    if ((st = upload_twiddles(p)) != CWT_OK) return bail(st);
+    if ((st = upload(p, &p->d_bs_chirp, chirp)) != CWT_OK) return bail(st);
+    if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return bail(st);
+    if ((st = dev_alloc(p, &p->d_bs_G, (size_t)(2 * P))) != CWT_OK) return bail(st);
+    if ((st = dev_alloc(p, &p->d_bs_work, (size_t)(3 * P))) != CWT_OK) return bail(st);
+    if (!p->fwd_small && (st = dev_alloc(p, &p->d_Y, (size_t)P)) != CWT_OK) return bail(st);
+    // D of the chirp sequences: [0] conj(c) (signal stage), [1] c (scales)
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(CWT_ERR_CUDA);
+    const Params B = base_params(p);
+    const unsigned gp = (unsigned)std::min<int64_t>((P + kBsThreads - 1) / kBsThreads, 4096);
+    for (int q = 0; q < 2 && st == CWT_OK; q++) {
+        BsArgs a{};
+        a.chirp = p->d_bs_chirp;
+        a.dst = p->d_bs_work;
+        a.N = N;
+        a.P = (int32_t)P;
+        a.conj_c = q == 0;
+        k_bs_seq<<<gp, kBsThreads, 0, s>>>(a);
+        if (cudaGetLastError() != cudaSuccess) st = CWT_ERR_CUDA;
+        Params Q = B;
+        Q.cin = p->d_bs_work;
+        Q.Fp_out = p->d_bs_G + q * P;
+        Q.cmode = 3;
+        Q.Y = p->d_Y;
+        if (st == CWT_OK) st = launch_forward(p, Q, s, 0.0, 0.0);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == CWT_OK) st = CWT_ERR_CUDA;
+    cudaStreamDestroy(s);
+    if (st != CWT_OK) return bail(st);
+    *plan = p;
+    return CWT_OK;
+}
+
 cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales,
                                     int32_t wavelet, const cwt_plan_opts& o) {
-    if (wavelet != CWT_WAVELET_GDW && wavelet != CWT_WAVELET_MORLET) return CWT_ERR_UNSUPPORTED;
     std::vector<double> wt(n_scales);
     for (int32_t i = 0; i < n_scales; i++) wt[i] = o.scale_unit == CWT_SCALE_DILATION ? 1.0 / scales[i] : scales[i];
-    double u_lo, u_hi;
-    wavelet_band(wavelet, o.omega0, 1e-7, &u_lo, &u_hi);
-    std::vector<int64_t> E(n_scales), Mr(n_scales);
+    // rows the extended-signal form cannot take (Mr = 0): other wavelets, scales
+    // whose spectrum is not negligible at the Nyquist frequency, and padded
+    // lengths beyond 2^kMaxLogM go to the Bluestein form (create_bluestein)
+    const bool ext_ok = wavelet == CWT_WAVELET_GDW || wavelet == CWT_WAVELET_MORLET;
+    double u_lo = 0.0, u_hi = 0.0;
+    if (ext_ok) wavelet_band(wavelet, o.omega0, 1e-7, &u_lo, &u_hi);
+    std::vector<int64_t> E(n_scales, 0), Mr(n_scales, 0);
     for (int32_t i = 0; i < n_scales; i++) {
+        if (!ext_ok) continue;
         const double nyq = kPi / wt[i];                  // u at the Nyquist frequency
-        if (u_hi >= nyq || u_lo <= -nyq) return CWT_ERR_UNSUPPORTED;
-        E[i] = edge_width(wavelet, wt[i]);
-        Mr[i] = int64_t(1) << ilog2(N + 3 * E[i]);
-        if (Mr[i] < N + 3 * E[i]) Mr[i] <<= 1;
-        if (Mr[i] > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
+        if (u_hi >= nyq || u_lo <= -nyq) continue;
+        const int64_t e = edge_width(wavelet, wt[i]);
+        int64_t m = int64_t(1) << ilog2(N + 3 * e);
+        if (m < N + 3 * e) m <<= 1;
+        if (m > (int64_t(1) << kMaxLogM)) continue;
+        E[i] = e;
+        Mr[i] = m;
     }
+    int64_t P = 4;                               // the Bluestein form's FFT length
+    while (P < 2 * N - 1) P <<= 1;
+    for (int32_t i = 0; i < n_scales; i++)
+        if (Mr[i] == 0 && P > (int64_t(1) << kMaxLogM)) return CWT_ERR_UNSUPPORTED;
     cwt_plan* p = new (std::nothrow) cwt_plan();
     if (!p) return CWT_ERR_OOM;
     p->N = N;
@@ -1318,23 +1527,31 @@ cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* sc
         while (r1 < n_scales && Mr[r1] == Mr[r0]) r1++;
         int64_t Eg = 0;
         for (int32_t i = r0; i < r1; i++) Eg = std::max(Eg, E[i]);
-        cwt_plan_opts so = o;
-        so.scale_unit = CWT_SCALE_W_TILDE;
-        so.fft_len = Mr[r0];
         cwt_plan* sub = nullptr;
-        cwt_status st = cwt_plan_create_ex(&sub, N + 2 * Eg, wt.data() + r0, r1 - r0, wavelet, CWT_BOUNDARY_ZERO, &so);
+        cwt_status st;
+        if (Mr[r0] == 0) {
+            // Bluestein rows read the signal itself (the extension's middle, E = 0)
+            st = create_bluestein(&sub, N, wt.data() + r0, r1 - r0, wavelet, o);
+        } else {
+            cwt_plan_opts so = o;
+            so.scale_unit = CWT_SCALE_W_TILDE;
+            so.fft_len = Mr[r0];
+            st = cwt_plan_create_ex(&sub, N + 2 * Eg, wt.data() + r0, r1 - r0, wavelet, CWT_BOUNDARY_ZERO, &so);
+            if (st == CWT_OK) {
+                sub->out_off = Eg;
+                sub->out_len = N;
+            }
+        }
         if (st != CWT_OK) {
             free_plan(p);
             return st;
         }
-        sub->out_off = Eg;
-        sub->out_len = N;
         p->subs.push_back(sub);
         p->sub_r0.push_back(r0);
         p->sub_E.push_back(Eg);
         p->ext_E = std::max(p->ext_E, Eg);
         p->ws_bytes += sub->ws_bytes;
-        p->M = std::max(p->M, Mr[r0]);
+        p->M = std::max(p->M, sub->M);
         r0 = r1;
     }
     p->logM = ilog2(p->M);

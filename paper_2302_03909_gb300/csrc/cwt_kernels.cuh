@@ -92,6 +92,13 @@ struct Params {
     int32_t yperm;           // wide pass 1: Y rows in the order of the tensor-core pass 2 (tc_rho)
     int32_t yz0;             // tensor-core pass 2: index of this launch's first Y slab in the plan's Y
     int32_t* err;            // tensor-core pass 2: set to 1 when a bounded wait gives up
+    // complex transforms of the forward kernels (the Bluestein path): with cin set,
+    // the forward reads M complex values from cin instead of the real signal and
+    // writes all M outputs, by cmode: 1 conj(X G), 2 conj(X), 3 X (X the e^{-} DFT)
+    const float2* cin;
+    const float2* cG;
+    int32_t cmode;
+    int32_t pad2_;
 };
 
 // Rows of the wide-scale intermediate in the order the tensor-core pass 2
@@ -844,22 +851,38 @@ struct SigFill {
     int b0, L;
     template <int R>
     __device__ __forceinline__ void operator()(float2 (&v)[R], int j, int t, int stride) {
+        if (p->cin) {
 #pragma unroll
-        for (int r = 0; r < R; r++) v[r] = make_float2(load_signal(*p, b0 + t + L * (j + r * stride)), 0.f);
+            for (int r = 0; r < R; r++) v[r] = __ldg(&p->cin[b0 + t + L * (j + r * stride)]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) v[r] = make_float2(load_signal(*p, b0 + t + L * (j + r * stride)), 0.f);
+        }
     }
 };
 
 // F(n) = conj X(n) for n = d0 + t + A c <= M/2 (the forward uses the paper's
-// e^{+} sign: sum_n f(n) e^{+2 pi i m n / M} = conj of the e^{-} DFT of real f)
+// e^{+} sign: sum_n f(n) e^{+2 pi i m n / M} = conj of the e^{-} DFT of real f).
+// Complex transforms (mode > 0) write every n < M: conj(X(n) G(n)), conj X(n)
+// or X(n).
 struct FOut {
     float2* F;
     int A, d0, half;
+    const float2* G;
+    int mode;
     template <int R>
     __device__ __forceinline__ void operator()(const float2 (&v)[R], int j, int t, int stride) {
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int n = d0 + t + A * (j + r * stride);
-            if (n <= half) F[n] = make_float2(v[r].x, -v[r].y);
+            if (mode == 0) {
+                if (n <= half) F[n] = make_float2(v[r].x, -v[r].y);
+            } else if (mode == 1) {
+                const float2 x = cmul(v[r], __ldg(&G[n]));
+                F[n] = make_float2(x.x, -x.y);
+            } else {
+                F[n] = mode == 2 ? make_float2(v[r].x, -v[r].y) : v[r];
+            }
         }
     }
 };
@@ -892,7 +915,7 @@ __device__ __forceinline__ void fwd2_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGL, MAXLR);
     extern __shared__ float2 smem[];
     const int d0 = c.x * T;
-    FOut out{p.Fp_out, p.A, d0, p.M >> 1};
+    FOut out{p.Fp_out, p.A, d0, p.M >> 1, p.cG, p.cmode};
     if (p.A == 1) {
         SigFill fill{&p, 0, 1};
         cta_fft<LOGL, T, NT, false, MAXLR>(smem, p.tw_tab, fill, out, 1);

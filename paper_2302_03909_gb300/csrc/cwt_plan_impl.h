@@ -86,6 +86,14 @@ struct cwt_plan {
     float2* d_tw_hi = nullptr;
     float2* d_tw_tab = nullptr;
     size_t ws_bytes = 0;
+    // periodic boundary for any N (Bluestein chirp transform; M = P >= 2N - 1
+    // the power-of-two FFT length): chirp c_j (N), D of the two chirp
+    // sequences ([0]: conj(c) for the signal, [1]: c for the scales; P each),
+    // work buffers (3 x P)
+    bool bs = false;
+    float2* d_bs_chirp = nullptr;
+    float2* d_bs_G = nullptr;
+    float2* d_bs_work = nullptr;
     // cwt_exec_host buffers
     void* h_sig = nullptr;
     void* h_W = nullptr;

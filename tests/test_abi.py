@@ -66,8 +66,10 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=64, scales=[2.0], dx=0.0), 1),
     (dict(N=64, scales=[2.0], eps_trunc=-1.0), 1),
     (dict(N=64, scales=[2.0], wavelet="morlet", omega0=0.0), 1),
-    (dict(N=100, scales=[2.0], boundary="periodic", wavelet="cbsw"), 2),   # periodic, N not 2^k: GDW/Morlet only
-    (dict(N=100, scales=[0.5], boundary="periodic"), 2),         # spectrum not negligible at Nyquist
+    # periodic, N not 2^k, rows of the Bluestein form (other wavelets, spectrum at the
+    # Nyquist frequency): FFT length 2^ceil(log2(2N - 1)) above 2^25
+    (dict(N=(1 << 24) + 1, scales=[2.0], boundary="periodic", wavelet="cbsw"), 2),
+    (dict(N=(1 << 24) + 1, scales=[0.5], boundary="periodic"), 2),
     (dict(N=64, scales=[2.0], boundary="zero", fft_len=32), 1),   # shorter than N
     (dict(N=64, scales=[2.0], boundary="zero", fft_len=96), 2),   # not 2^k
     (dict(N=64, scales=[2.0], boundary="periodic", fft_len=128), 1),

@@ -140,3 +140,34 @@ def test_batch_argument_checks(env):
     assert lib.cwt_batch_destroy(None) == 0
     for p, *_ in items:
         p.close()
+
+
+def test_batch_with_bluestein_plans(env):
+    """Periodic plans of lengths that are not powers of two, with rows of the
+    Bluestein form (CBSW, CW-GDW, a scale whose spectrum reaches the Nyquist
+    frequency) beside extended-signal rows, in one batch: bit-equal to direct
+    calls."""
+    torch, cwt = env
+    specs = [(1000, "cbsw", 1.0, 250.0, 7), (3001, "cwgdw", 1.0, 700.0, 6), (1023, "morlet", 0.6, 300.0, 6),
+             (5000, "gdw", 0.5, 1200.0, 8)]
+    items = []
+    for i, (N, wav, lo, hi, S) in enumerate(specs):
+        p = cwt.cwt_plan_create(N, synth.log_scales(lo, hi, S), wav, "periodic")
+        sig = torch.tensor(synth.multitone(N, seed=40 + i), dtype=torch.float32, device="cuda")
+        items.append((p, sig, p.empty_output("cuda"), torch.empty(S, dtype=torch.float64, device="cuda")))
+    ref = _reference(torch, cwt, items)
+    b = cwt.cwt_batch_create(items, n_streams=3)
+    st = torch.cuda.Stream()
+    for _, _, W, sp in items:
+        W.fill_(float("nan"))
+        sp.fill_(float("nan"))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        b.exec(st)
+    torch.cuda.synchronize()
+    for (W0, s0), (p, _, W, sp) in zip(ref, items):
+        assert torch.equal(W, W0), p.N
+        assert torch.equal(sp, s0), p.N
+    b.close()
+    for p, *_ in items:
+        p.close()

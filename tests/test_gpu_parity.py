@@ -383,10 +383,21 @@ def test_zero_boundary_short_scales(env, N, wavelet, smin, smax, S, order, dtype
     (997, "morlet", 4.0, 900.0, 7, "shuffled", "f32"),        # prime N, scales beyond N/4
     (4097, "gdw", 2.0, 1000.0, 10, "desc", "f64"),
     (100000, "morlet", 4.0, 25000.0, 12, "asc", "f32"),
+    # rows of the Bluestein form: the other wavelets, and scales whose spectrum
+    # reaches the Nyquist frequency (mixed with extended-signal rows)
+    (1000, "cbsw", 1.0, 250.0, 9, "asc", "f32"),
+    (3001, "cwgdw", 1.0, 700.0, 10, "shuffled", "f64"),
+    (1023, "morlet", 0.6, 300.0, 8, "asc", "f32"),
+    (1000, "gdw", 0.5, 250.0, 9, "desc", "f32"),
+    (7, "gdw", 0.7, 2.0, 3, "asc", "f32"),                       # P = 16: one CTA
+    (5000, "cbsw", 2.0, 1200.0, 6, "asc", "f32"),                # P = 16384: two passes
+    (100003, "cwgdw", 1.0, 20000.0, 8, "asc", "f32"),            # P = 262144
 ])
 def test_periodic_any_length(env, N, wavelet, smin, smax, S, order, dtype):
     """Periodic boundary with N not a power of two: W and the power spectrum
-    against the oracle's N-point FFTCWT (its own Bluestein FFT)."""
+    against the oracle's N-point FFTCWT (its own Bluestein FFT).  Rows go to the
+    extended-signal form or, where it does not apply, to the library's
+    Bluestein form."""
     _, _, orc = env
     f = synth.lognormal_field(N, seed=N + 3)
     sc = synth.log_scales(smin, smax, S)
