@@ -1008,9 +1008,9 @@ cwt_status host_copy_rows(cwt_plan* p, cudaStream_t s, std::vector<int> rows) {
 cwt_status run_bluestein(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     using BsFn = void (*)(BsArgs);
     const int64_t P = p->M;
-    float2* X = p->d_bs_work;
+    float2* Cv = p->d_bs_work;                   // then X, X2 of each stream
+    float2* X = Cv + P;
     float2* X2 = X + P;
-    float2* Cv = X + 2 * P;
     const Params B = base_params(p);
     BsArgs a{};
     a.signal = signal;
@@ -1027,42 +1027,63 @@ cwt_status run_bluestein(cwt_plan* p, const void* signal, void* W, double* spect
     a.inv_p = (float)(1.0 / (double)P);
     const unsigned gp = (unsigned)std::min<int64_t>((P + kBsThreads - 1) / kBsThreads, 4096);
     const unsigned go = (unsigned)((p->N + kBsOutBlock - 1) / kBsOutBlock);
-    auto elem = [&](BsFn fn, const void* gfn, unsigned grid, int cls, double bytes) -> cwt_status {
+    auto elem = [&](BsFn fn, const void* gfn, unsigned grid, cudaStream_t es, int cls, double bytes) -> cwt_status {
         if (p->rec) {
-            rec_launch(p, gfn, dim3(grid), dim3(kBsThreads), 0, s, a);
+            rec_launch(p, gfn, dim3(grid), dim3(kBsThreads), 0, es, a);
             return CWT_OK;
         }
-        LaunchTimer lt(p, cls, bytes, s);
-        fn<<<grid, kBsThreads, 0, s>>>(a);
+        LaunchTimer lt(p, cls, bytes, es);
+        fn<<<grid, kBsThreads, 0, es>>>(a);
         CWT_CUDA(p, cudaGetLastError());
         lt.done();
         return CWT_OK;
     };
-    auto fft = [&](const float2* in, float2* out, const float2* G, int mode) -> cwt_status {
+    auto fft = [&](const float2* in, float2* out, const float2* G, int mode, float2* Y, cudaStream_t es) -> cwt_status {
         Params Q = B;
         Q.cin = in;
         Q.Fp_out = out;
         Q.cG = G;
         Q.cmode = mode;
-        Q.Y = p->d_Y;
-        return launch_forward(p, Q, s, 8.0 * (double)P, 8.0 * (double)P);
+        Q.Y = Y;
+        return launch_forward(p, Q, es, 8.0 * (double)P, 8.0 * (double)P);
     };
     cwt_status st;
     a.dst = X;
-    if ((st = elem(k_bs_sig, (const void*)k_bs_sig_g, gp, CWT_KCLASS_FORWARD, 4.0 * (double)p->N)) != CWT_OK) return st;
-    if ((st = fft(X, X2, p->d_bs_G, 1)) != CWT_OK) return st;
-    if ((st = fft(X2, Cv, nullptr, 2)) != CWT_OK) return st;
-    for (const Job& J : p->jobs) {
-        a.J = J;
+    if ((st = elem(k_bs_sig, (const void*)k_bs_sig_g, gp, s, CWT_KCLASS_FORWARD, 4.0 * (double)p->N)) != CWT_OK)
+        return st;
+    if ((st = fft(X, X2, p->d_bs_G, 1, p->d_Y, s)) != CWT_OK) return st;
+    if ((st = fft(X2, Cv, nullptr, 2, p->d_Y, s)) != CWT_OK) return st;
+    // the jobs are independent: round robin over the call's stream and the side
+    // streams, each with its own X, X2 and forward intermediate
+    const int nst = p->timing == 2 ? 1 : std::min<int>((int)p->jobs.size(), p->bs_streams);
+    cudaStream_t streams[cwt_plan::kSide + 1] = {s};
+    if (nst > 1) {
+        if ((st = ev_record(p, p->ev_fork, s)) != CWT_OK) return st;
+        for (int i = 1; i < nst; i++) {
+            streams[i] = p->side[i - 1];
+            if ((st = ev_wait(p, streams[i], p->ev_fork)) != CWT_OK) return st;
+        }
+    }
+    for (size_t j = 0; j < p->jobs.size(); j++) {
+        const int si = (int)(j % nst);
+        cudaStream_t es = streams[si];
+        float2* Xs = X + 2 * P * si;
+        float2* X2s = Xs + P;
+        float2* Ys = p->d_Y ? p->d_Y + P * si : nullptr;
+        a.J = p->jobs[j];
         a.src = Cv;
-        a.dst = X;
-        if ((st = elem(k_bs_scale, (const void*)k_bs_scale_g, gp, CWT_KCLASS_WIDE1, 0.0)) != CWT_OK) return st;
-        if ((st = fft(X, X2, p->d_bs_G + P, 1)) != CWT_OK) return st;
-        if ((st = fft(X2, X, nullptr, 2)) != CWT_OK) return st;
-        a.src = X;
-        if ((st = elem(k_bs_out, (const void*)k_bs_out_g, go, CWT_KCLASS_WIDE2, job_rows(J) * out_row_bytes(p))) !=
-            CWT_OK)
+        a.dst = Xs;
+        if ((st = elem(k_bs_scale, (const void*)k_bs_scale_g, gp, es, CWT_KCLASS_WIDE1, 0.0)) != CWT_OK) return st;
+        if ((st = fft(Xs, X2s, p->d_bs_G + P, 1, Ys, es)) != CWT_OK) return st;
+        if ((st = fft(X2s, Xs, nullptr, 2, Ys, es)) != CWT_OK) return st;
+        a.src = Xs;
+        if ((st = elem(k_bs_out, (const void*)k_bs_out_g, go, es, CWT_KCLASS_WIDE2,
+                       job_rows(a.J) * out_row_bytes(p))) != CWT_OK)
             return st;
+    }
+    for (int i = 1; i < nst; i++) {
+        if ((st = ev_record(p, p->ev_join[i - 1], streams[i])) != CWT_OK) return st;
+        if ((st = ev_wait(p, s, p->ev_join[i - 1])) != CWT_OK) return st;
     }
     if (spectrum) {
         LaunchTimer lt(p, CWT_KCLASS_POWER, 8.0 * (double)(p->n_partials + p->S), s);
@@ -1453,8 +1474,14 @@ cwt_status create_bluestein(cwt_plan** plan, int64_t N, const double* wt, int32_
     if ((st = upload(p, &p->d_bs_chirp, chirp)) != CWT_OK) return bail(st);
     if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return bail(st);
     if ((st = dev_alloc(p, &p->d_bs_G, (size_t)(2 * P))) != CWT_OK) return bail(st);
-    if ((st = dev_alloc(p, &p->d_bs_work, (size_t)(3 * P))) != CWT_OK) return bail(st);
-    if (!p->fwd_small && (st = dev_alloc(p, &p->d_Y, (size_t)P)) != CWT_OK) return bail(st);
+    p->bs_streams = std::min<int>((int)p->jobs.size(), cwt_plan::kSide + 1);
+    if ((st = dev_alloc(p, &p->d_bs_work, (size_t)(P + 2 * P * p->bs_streams))) != CWT_OK) return bail(st);
+    if (!p->fwd_small && (st = dev_alloc(p, &p->d_Y, (size_t)(P * p->bs_streams))) != CWT_OK) return bail(st);
+    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return bail(CWT_ERR_CUDA);
+    for (int i = 0; i < cwt_plan::kSide; i++)
+        if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(CWT_ERR_CUDA);
     // D of the chirp sequences: [0] conj(c) (signal stage), [1] c (scales)
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(CWT_ERR_CUDA);
@@ -1463,14 +1490,14 @@ cwt_status create_bluestein(cwt_plan** plan, int64_t N, const double* wt, int32_
     for (int q = 0; q < 2 && st == CWT_OK; q++) {
         BsArgs a{};
         a.chirp = p->d_bs_chirp;
-        a.dst = p->d_bs_work;
+        a.dst = p->d_bs_work + P;
         a.N = N;
         a.P = (int32_t)P;
         a.conj_c = q == 0;
         k_bs_seq<<<gp, kBsThreads, 0, s>>>(a);
         if (cudaGetLastError() != cudaSuccess) st = CWT_ERR_CUDA;
         Params Q = B;
-        Q.cin = p->d_bs_work;
+        Q.cin = p->d_bs_work + P;
         Q.Fp_out = p->d_bs_G + q * P;
         Q.cmode = 3;
         Q.Y = p->d_Y;

@@ -89,8 +89,9 @@ struct cwt_plan {
     // periodic boundary for any N (Bluestein chirp transform; M = P >= 2N - 1
     // the power-of-two FFT length): chirp c_j (N), D of the two chirp
     // sequences ([0]: conj(c) for the signal, [1]: c for the scales; P each),
-    // work buffers (3 x P)
+    // work buffers (conv1, then X and X2 of each stream; P each)
     bool bs = false;
+    int bs_streams = 1;                   // streams the jobs are spread over (per-stream X, X2 and Y)
     float2* d_bs_chirp = nullptr;
     float2* d_bs_G = nullptr;
     float2* d_bs_work = nullptr;
