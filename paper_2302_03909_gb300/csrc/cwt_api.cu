@@ -1122,13 +1122,25 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
                 lt.done();
             }
         }
+        // recording a batch: the sub-plans (disjoint rows) each on a stream of
+        // their own, forked after the extension, joined by the call's stream
+        const int sub_fork = p->rec ? p->rec->level_of((const void*)s) : 0;
+        int sub_level = sub_fork;
         for (size_t i = 0; i < p->subs.size(); i++) {
             const void* sig = ext ? (const void*)((const char*)p->d_ext + (size_t)(p->ext_E - p->sub_E[i]) * se)
                                   : signal;
             void* Wi = (char*)W + (size_t)p->sub_r0[i] * (size_t)p->N * we;
             double* spi = spectrum ? spectrum + p->sub_r0[i] : nullptr;
-            if ((st = run_launches(p->subs[i], sig, Wi, spi, s)) != CWT_OK) return st;
+            cudaStream_t ss = s;
+            if (p->rec) {
+                const void* key = &p->subs[i];
+                p->rec->stream_level[key] = sub_fork;
+                ss = (cudaStream_t)key;
+            }
+            if ((st = run_launches(p->subs[i], sig, Wi, spi, ss)) != CWT_OK) return st;
+            if (p->rec) sub_level = std::max(sub_level, p->rec->level_of((const void*)ss));
         }
+        if (p->rec) p->rec->stream_level[(const void*)s] = std::max(p->rec->level_of((const void*)s), sub_level);
         return CWT_OK;
     }
     Params P = base_params(p);
@@ -1294,6 +1306,11 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         }
         if ((st = host_copy_rows(p, ws, rows_of_jobs(p, wb.job0, wb.count))) != CWT_OK) return st;
     }
+    // recording a batch: every band group on a stream of its own (a key only the
+    // recorder sees), forked where the band work may start, so that independent
+    // groups share one dependency level; the call's stream joins them all
+    const int fork_level = p->rec ? p->rec->level_of((const void*)s) : 0;
+    int band_level = fork_level;
     for (size_t gi = 0; gi < p->groups.size(); gi++) {
         const auto& g = p->groups[gi];
         const Entry& e = g.rdi ? tb.band_rd[g.rdi][p->crop] : tb.band[g.logl][p->crop];
@@ -1303,9 +1320,16 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         Q.D = g.D;
         size_t smem = (size_t)((1 << g.rdi) << g.logl) * sizeof(float2) + stage_smem(g.logl, e.T);
         cudaStream_t gs = streams[next++ % nstreams];
+        if (p->rec) {
+            const void* key = &p->groups[gi];
+            p->rec->stream_level[key] = fork_level;
+            gs = (cudaStream_t)key;
+        }
         if ((st = launch(p, e, dim3(g.ntiles), smem, Q, gs, CWT_KCLASS_BAND, g.bytes)) != CWT_OK) return st;
+        if (p->rec) band_level = std::max(band_level, p->rec->level_of((const void*)gs));
         if ((st = host_copy_rows(p, gs, rows_of_jobs(p, g.job0, g.njobs))) != CWT_OK) return st;
     }
+    if (p->rec) p->rec->stream_level[(const void*)s] = std::max(p->rec->level_of((const void*)s), band_level);
     for (int i = 1; i < nstreams; i++) {
         if ((st = ev_record(p, p->ev_join[i - 1], streams[i])) != CWT_OK) return st;
         if ((st = ev_wait(p, s, p->ev_join[i - 1])) != CWT_OK) return st;
