@@ -1421,9 +1421,14 @@ cwt_status plan_check_device(cwt_plan* p) { return check_device(p); }
 // Periodic boundary with N not a power of two (GDW, Morlet).  A scale whose
 // wavelet is negligible beyond E samples gives the same W on [0, N) as the
 // zero-boundary transform of the signal extended periodically by E samples on
-// each side, kept on [E, E + N), when the padded length is at least N + 3E
-// (the window sees no wrap-around).  Consecutive rows sharing the power-of-two
-// length M >= N + 3E form one zero-boundary sub-plan of fft_len M.  Scales
+// each side, kept on [E, E + N), when the padded length M is at least
+// N + 2E + 1: an output n in the window reads the extended samples n - E ..
+// n + E directly, and its wrapped neighbours n + t - M (|t| <= E) fall below
+// index 0 while n + t + M lies beyond the extension's N + 2E samples.  (Every
+// output of the extended signal would need N + 3E + 1; only the window is
+// kept.)  Consecutive rows sharing the power-of-two length M >= N + 2E + 1 form
+// one zero-boundary sub-plan of fft_len M; a row of the group with a shorter
+// support E' <= E needs less.  Scales
 // whose spectrum is not negligible (1e-7 of its peak) at the Nyquist frequency
 // are refused: their band-limited wavelet rings instead of decaying.
 // Periodic boundary for any N, every wavelet and every scale: the N-point
@@ -1550,8 +1555,7 @@ cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* sc
         const double nyq = kPi / wt[i];                  // u at the Nyquist frequency
         if (u_hi >= nyq || u_lo <= -nyq) continue;
         const int64_t e = edge_width(wavelet, wt[i]);
-        int64_t m = int64_t(1) << ilog2(N + 3 * e);
-        if (m < N + 3 * e) m <<= 1;
+        const int64_t m = int64_t(1) << ilog2(N + 2 * e + 1);
         if (m > (int64_t(1) << kMaxLogM)) continue;
         E[i] = e;
         Mr[i] = m;
