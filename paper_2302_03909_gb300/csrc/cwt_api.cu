@@ -348,9 +348,11 @@ static __global__ void k_edge_power_g(GroupMap g) {
 
 namespace {
 
-// half width (in units of x) beyond which |psi(x)| < ~1e-13: GDW (2 - x^2) e^{-x^2/4}
-// at x = 12.5, the Morlet's Gaussian envelope e^{-x^2/2} at x = 8.5
-double psi_support(int wavelet) { return wavelet == CWT_WAVELET_GDW ? 12.5 : 8.5; }
+// half width (in units of x) beyond which |psi(x)| < 1e-9 of its peak: the GDW's
+// (x^2 - 2) e^{-x^2/4} / 2 is 6.8e-10 at x = 10, the Morlet's envelope e^{-x^2/2}
+// 6.7e-10 at x = 6.5.  Terms beyond it change W by ~1e-10 relative, far below
+// the FP32 path's own rounding.
+double psi_support(int wavelet) { return wavelet == CWT_WAVELET_GDW ? 10.0 : 6.5; }
 
 int64_t edge_width(int wavelet, double wt) { return (int64_t)std::ceil(psi_support(wavelet) / wt) + 1; }
 

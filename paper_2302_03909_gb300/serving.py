@@ -219,8 +219,8 @@ def workspace_bound(N: int, scales, wavelet: str, boundary: str) -> int:
     boundary pads to M = pow2 >= 2N, with a periodic N-point child plan when N
     is a power of two and shorter sub-plans (M/2 and M) otherwise; the
     periodic boundary uses M = N for a power of two, else sub-plans of length
-    pow2 >= N + 3E per row (E = ceil(chi s) + 1 the dilated wavelet's support,
-    chi = 12.5 for the GDW and 8.5 for the Morlet) over a buffer of
+    pow2 >= N + 2E + 1 per row (E = ceil(chi s) + 1 the dilated wavelet's
+    support, chi = 10 for the GDW and 6.5 for the Morlet) over a buffer of
     N + 2 max E samples."""
     S = len(scales)
     if boundary == "zero":
@@ -228,9 +228,9 @@ def workspace_bound(N: int, scales, wavelet: str, boundary: str) -> int:
         return _plan_bound(M, S) + (_plan_bound(N, S) if N == _pow2(N) else _plan_bound(M // 2, S))
     if N == _pow2(N):
         return _plan_bound(N, S)
-    chi = 12.5 if wavelet == "gdw" else 8.5
+    chi = 10.0 if wavelet == "gdw" else 6.5
     E = [int(math.ceil(chi * float(sv))) + 1 for sv in scales]
-    Ms = sorted({_pow2(N + 3 * e) for e in E})
+    Ms = sorted({_pow2(N + 2 * e + 1) for e in E})
     return sum(_plan_bound(M, S) for M in Ms) + 8 * (N + 2 * max(E))
 
 
