@@ -81,6 +81,8 @@ def parse_args():
     # serving: a Poisson trace of requests through paper_2302_03909_gb300.serving
     ap.add_argument("--serving", action="store_true", help="measure request latency instead of throughput")
     ap.add_argument("--rate", type=float, default=500.0, help="serving: requests per second")
+    ap.add_argument("--serving-lengths", default="pow2", choices=["integer", "pow2"],
+                    help="serving: signal lengths log-uniform integers (2 per octave) or powers of two")
     ap.add_argument("--seconds", type=float, default=5.0, help="serving: length of the arrival trace")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests in flight at once")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
@@ -408,7 +410,8 @@ def run_reference(args):
 
 
 def run_serving(args, embedded=False):
-    """Poisson arrivals (N = 2^10..2^24, 16..128 scales, GDW or Morlet, periodic or
+    """Poisson arrivals (N in 2^10..2^24: log-uniform integers from a pool of two
+    per octave, or powers of two; 16..128 scales, GDW or Morlet, periodic or
     zero boundary) served with ``--slots`` streams, then the same trace with one
     slot (serial execution); plans of every request shape are created first
     (a resident plan cache).  Prints one JSON line of latency percentiles."""
@@ -417,11 +420,12 @@ def run_serving(args, embedded=False):
     from paper_2302_03909_gb300 import serving
 
     torch.cuda.set_device(0)
-    trace = serving.poisson_trace(args.rate, args.seconds)
+    per_octave = 2 if args.serving_lengths == "integer" else 0
+    trace = serving.poisson_trace(args.rate, args.seconds, integer_lengths=per_octave)
     pool = {}
     for r in trace:
         if r.N not in pool:
-            pool[r.N] = torch.tensor(synth.lognormal_field(r.N, seed=synth.BASE_SEED + 50 + r.N.bit_length()),
+            pool[r.N] = torch.tensor(synth.lognormal_field(r.N, seed=synth.BASE_SEED + 50 + r.N % 100003),
                                      dtype=torch.float32).pin_memory()
         r.signal = pool[r.N]
     budget = int(args.budget_gb * (1 << 30))
@@ -455,7 +459,9 @@ def run_serving(args, embedded=False):
             "concurrent": out["concurrent"], "concurrent_fifo": out["concurrent_fifo"], "serial": out["serial"],
             "config": {"rate_per_s": args.rate, "seconds": args.seconds, "requests": len(trace),
                        "slots": args.slots, "policy": args.policy, "budget_gb": args.budget_gb,
-                       "N": "2^10..2^24 (powers of two)",
+                       "N": ("log-uniform integers in 2^10..2^24 (a pool of 2 per octave, mostly not powers "
+                             "of two)" if per_octave else "2^10..2^24 (powers of two)"),
+                       "distinct_shapes": len({r.key for r in trace}),
                        "n_scales": "16..128", "wavelets": ["gdw", "morlet"], "boundaries": ["periodic", "zero"],
                        "plans": "resident, created before the trace",
                        "buffers": "new per request" if args.fresh_buffers

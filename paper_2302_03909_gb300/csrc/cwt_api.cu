@@ -389,12 +389,19 @@ struct ExtendArgs {
     int64_t N, E;
     int32_t f64, pad_;
 };
+// One modulo per thread: the source index then advances by the grid stride
+// reduced mod N, wrapping with one subtraction.
 __device__ __forceinline__ void periodic_extend_body(const ExtendArgs& a, const Cta c) {
     const int64_t N = a.N, E = a.E, total = N + 2 * E;
-    for (int64_t m = c.x * (int64_t)blockDim.x + threadIdx.x; m < total; m += (int64_t)c.nx * blockDim.x) {
-        const int64_t src = ((m - E) % N + N) % N;
+    const int64_t stride = (int64_t)c.nx * blockDim.x, step = stride % N;
+    int64_t m = c.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= total) return;
+    int64_t src = ((m - E) % N + N) % N;
+    for (; m < total; m += stride) {
         if (a.f64) ((double*)a.ext)[m] = __ldg(&((const double*)a.f)[src]);
         else ((float*)a.ext)[m] = __ldg(&((const float*)a.f)[src]);
+        src += step;
+        if (src >= N) src -= N;
     }
 }
 static __global__ void k_periodic_extend(ExtendArgs a) { periodic_extend_body(a, cta_plain()); }
@@ -1114,7 +1121,8 @@ cwt_status run_launches(cwt_plan* p, const void* signal, void* W, double* spectr
         if (ext) {
             LaunchTimer lt(p, CWT_KCLASS_FORWARD, 0.0, s);
             const int64_t total = p->N + 2 * p->ext_E;
-            const unsigned blocks = (unsigned)std::min<int64_t>(4096, (total + 255) / 256);
+            // about 8 samples per thread: the per-thread modulo is then amortised
+            const unsigned blocks = (unsigned)std::min<int64_t>(4096, (total + 2047) / 2048);
             const ExtendArgs a{signal, p->d_ext, p->N, p->ext_E, f64, 0};
             if (p->rec) {
                 rec_launch(p, (const void*)k_periodic_extend_g, dim3(blocks), dim3(256), 0, s, a);

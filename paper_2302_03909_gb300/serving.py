@@ -436,23 +436,44 @@ def run_trace(server: Server, trace: List[Request], max_seconds: float = 600.0) 
             "plan_evictions": server.cache.evictions}
 
 
+def length_pool(log2n=(10, 24), per_octave: int = 2, seed: int = 20230214) -> List[int]:
+    """``per_octave`` integer lengths drawn log-uniformly in each octave
+    [2^u, 2^(u+1)) for u in [log2n[0], log2n[1]), plus 2^log2n[1]: a
+    service's set of signal lengths, mostly not powers of two."""
+    rng = np.random.default_rng(seed)
+    out = set()
+    for u in range(log2n[0], log2n[1]):
+        for _ in range(per_octave):
+            out.add(int(min(2 ** (u + 1) - 1, round(2.0 ** (u + rng.uniform(0.0, 1.0))))))
+    out.add(1 << log2n[1])
+    return sorted(out)
+
+
 def poisson_trace(rate: float, seconds: float, seed: int = 20230213, log2n=(10, 24), n_scales=(16, 128),
-                  shapes_per_log2n: int = 4) -> List[Request]:
+                  shapes_per_log2n: int = 4, integer_lengths: int = 0) -> List[Request]:
     """Poisson arrivals at ``rate`` per second for ``seconds``.  Each request:
-    N = 2^u with u uniform over log2n (power-of-two lengths, so both
-    boundaries apply), a scale count drawn from ``shapes_per_log2n`` values
-    spread over n_scales (requests of one service repeat shapes, which the
-    plan cache exploits), log-spaced dilations from 4 to N/4, the GDW or the
-    Morlet and the periodic or zero boundary with equal odds."""
+    N = 2^u with u uniform over log2n (power-of-two lengths), or, with
+    ``integer_lengths`` > 0, N drawn log-uniformly from ``length_pool`` with
+    that many integer lengths per octave; a scale count drawn from
+    ``shapes_per_log2n`` values spread over n_scales (requests of one service
+    repeat shapes, which the plan cache exploits), log-spaced dilations from 4
+    to N/4, the GDW or the Morlet and the periodic or zero boundary with equal
+    odds."""
     rng = np.random.default_rng(seed)
     t, out, rid = 0.0, [], 0
     counts = np.unique(np.linspace(n_scales[0], n_scales[1], shapes_per_log2n).astype(int))
+    pool = np.array(length_pool(log2n, integer_lengths)) if integer_lengths > 0 else None
     while True:
         t += rng.exponential(1.0 / rate)
         if t > seconds:
             break
-        u = int(rng.integers(log2n[0], log2n[1] + 1))
-        N = 1 << u
+        if pool is not None:
+            # log-uniform over the pool's range: the pool entry nearest (in log) to 2^u
+            x = rng.uniform(log2n[0], log2n[1])
+            N = int(pool[np.argmin(np.abs(np.log2(pool) - x))])
+        else:
+            u = int(rng.integers(log2n[0], log2n[1] + 1))
+            N = 1 << u
         S = int(rng.choice(counts))
         sc = tuple(float(x) for x in np.exp(np.linspace(np.log(4.0), np.log(max(8.0, N / 4)), S)))
         out.append(Request(rid, N, sc, "gdw" if rng.random() < 0.5 else "morlet",
