@@ -145,8 +145,24 @@ typedef struct {
                             DFT threads).  0: chosen per plan, 1 for transform lengths
                             M >= 2^21, 2 below.  The reduced precisions always take the tile
                             pipeline (tensor-core stages) */
-    int32_t reserved_;   /* must be 0 */
+    int32_t scratch;     /* cwt_scratch_mode: where the per-call buffers live (default
+                            CWT_SCRATCH_PLAN).  CWT_SCRATCH_CALLER plans keep only their constant
+                            tables and run with cwt_exec_scratch; they cannot be tuned */
 } cwt_plan_opts;
+
+/* Per-call buffers of a plan (the spectrum and its transposed copy, the wide
+ * scales' intermediate, power partial sums, the periodic extension, the edge
+ * corrections' partial sums, the Bluestein form's work arrays).
+ *   CWT_SCRATCH_PLAN   - allocated with the plan, one set per plan;
+ *   CWT_SCRATCH_CALLER - supplied by the caller on every call
+ *                        (cwt_exec_scratch), so that plans of many shapes can
+ *                        share one buffer per stream (a request server keeps
+ *                        one per slot).  Sub-plans of one plan run one after
+ *                        another and share offsets inside it. */
+typedef enum {
+    CWT_SCRATCH_PLAN = 0,
+    CWT_SCRATCH_CALLER = 1
+} cwt_scratch_mode;
 
 void cwt_plan_opts_default(cwt_plan_opts* opts);
 
@@ -184,6 +200,23 @@ cwt_status cwt_exec(cwt_plan* plan, const void* signal_dev, void* W_dev, void* s
  * so repeated calls give bit-identical spectra. */
 cwt_status cwt_exec_with_power(cwt_plan* plan, const void* signal_dev, void* W_dev,
                                double* spectrum_dev, void* stream);
+
+/* Bytes of caller-supplied scratch a CWT_SCRATCH_CALLER plan needs per call
+ * (0 for a CWT_SCRATCH_PLAN plan). */
+cwt_status cwt_plan_scratch_bytes(const cwt_plan* plan, size_t* bytes);
+
+/* cwt_exec_with_power for a CWT_SCRATCH_CALLER plan: the call's per-call
+ * buffers are carved from scratch_dev (device, 256 B aligned, at least
+ * cwt_plan_scratch_bytes bytes).  The scratch must not be used by anything
+ * else until the call's work on `stream` has finished; the plan keeps no
+ * pointer into it past the call.  spectrum_dev may be NULL.  Errors:
+ * CWT_ERR_INVALID_ARG for a plan with its own scratch, a NULL, misaligned or
+ * short scratch, or bad buffers.  CWT_SCRATCH_CALLER plans take no other
+ * transform call (cwt_exec, cwt_exec_with_power, cwt_exec_host and
+ * cwt_batch_create return CWT_ERR_INVALID_ARG); cwt_wavelet_power,
+ * cwt_env_power and cwt_icwt work as for any plan. */
+cwt_status cwt_exec_scratch(cwt_plan* plan, const void* signal_dev, void* W_dev, double* spectrum_dev,
+                            void* scratch_dev, size_t scratch_bytes, void* stream);
 
 /* Eq. 42 from a W array already in device memory (layout as cwt_exec writes it):
  * one read of W, fixed-order reduction, float64 output (device). */

@@ -25,7 +25,7 @@ __all__ = [
     "cwt_scales_paper_grid",
     "cwt_status_string", "cwt_wavelet_power_noalloc", "cwt_plan_set_timing", "cwt_plan_get_timing", "load_library",
     "Batch", "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy", "cwt_plan_get_opts",
-    "ABI_FUNCTIONS", "KERNEL_CLASSES",
+    "cwt_plan_scratch_bytes", "cwt_exec_scratch", "ABI_FUNCTIONS", "KERNEL_CLASSES",
 ]
 
 WAVELETS = {"gdw": 0, "mexhat": 0, "morlet": 1, "cbsw": 2, "cwgdw": 3}
@@ -41,6 +41,7 @@ ABI_FUNCTIONS = [
     "cwt_scales_paper_grid", "cwt_status_string", "cwt_plan_last_error", "cwt_plan_set_timing",
     "cwt_plan_get_timing", "cwt_wavelet_power_noalloc", "cwt_env_power", "cwt_icwt",
     "cwt_batch_create", "cwt_batch_exec", "cwt_batch_info", "cwt_batch_destroy", "cwt_plan_get_opts",
+    "cwt_plan_scratch_bytes", "cwt_exec_scratch",
 ]
 NOALLOC_MAX_PARTIALS = 65536
 NOALLOC_CHUNK = 32768
@@ -54,7 +55,9 @@ class _Opts(ctypes.Structure):
                 ("min_ctas", ctypes.c_int32), ("tune", ctypes.c_int32),
                 ("wide_batch_bytes", ctypes.c_int64), ("precision", ctypes.c_int32),
                 ("band_depth", ctypes.c_int32), ("wide2_kernel", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("scratch", ctypes.c_int32)]
+
+SCRATCH_MODES = {"plan": 0, "caller": 1}
 
 
 class CwtError(RuntimeError):
@@ -125,6 +128,10 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.cwt_batch_destroy.argtypes = [vp]
         lib.cwt_plan_get_opts.restype = ctypes.c_int
         lib.cwt_plan_get_opts.argtypes = [vp, ctypes.POINTER(_Opts)]
+        lib.cwt_plan_scratch_bytes.restype = ctypes.c_int
+        lib.cwt_plan_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.cwt_exec_scratch.restype = ctypes.c_int
+        lib.cwt_exec_scratch.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         _lib = lib
         return lib
 
@@ -195,7 +202,8 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
                     omega0: float = 6.0, dx: float = 1.0, scale_unit: str = "dilation",
                     input_dtype: str = "f32", fft_len: int = 0, eps_trunc: float = 1e-10,
                     min_ctas: int = 0, tune: bool = False, wide_batch_bytes: int = 0,
-                    precision: str = "fp32", band_depth: int = 0, wide2_kernel: int = 0) -> Plan:
+                    precision: str = "fp32", band_depth: int = 0, wide2_kernel: int = 0,
+                    scratch: str = "plan") -> Plan:
     lib = load_library()
     sc = np.ascontiguousarray(scales, dtype=np.float64)
     opts = _Opts()
@@ -211,6 +219,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     opts.precision = PRECISIONS[precision]
     opts.band_depth = int(band_depth)
     opts.wide2_kernel = int(wide2_kernel)
+    opts.scratch = SCRATCH_MODES[scratch]
     h = ctypes.c_void_p()
     st = lib.cwt_plan_create_ex(ctypes.byref(h), int(N),
                                 sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sc),
@@ -218,7 +227,7 @@ def cwt_plan_create(N: int, scales, wavelet: str = "gdw", boundary: str = "perio
     _check(st)
     return Plan(h, int(N), len(sc), wavelet, boundary,
                 dict(omega0=omega0, dx=dx, scale_unit=scale_unit, input_dtype=input_dtype,
-                     fft_len=fft_len, eps_trunc=eps_trunc, precision=precision))
+                     fft_len=fft_len, eps_trunc=eps_trunc, precision=precision, scratch=scratch))
 
 
 def cwt_plan_get_opts(plan: Plan) -> dict:
@@ -287,6 +296,29 @@ def cwt_exec_with_power(plan: Plan, signal, W=None, spectrum=None, stream=None):
     _check(load_library().cwt_exec_with_power(plan._h, _dev_ptr(signal, "signal"), _dev_ptr(W, "W"),
                                               _dev_ptr(spectrum, "spectrum"), _stream_ptr(stream)),
            plan)
+    return W, spectrum
+
+
+def cwt_plan_scratch_bytes(plan: Plan) -> int:
+    """Bytes of caller scratch a plan made with scratch="caller" needs per call (0 otherwise)."""
+    n = ctypes.c_size_t()
+    _check(load_library().cwt_plan_scratch_bytes(plan._h, ctypes.byref(n)), plan)
+    return n.value
+
+
+def cwt_exec_scratch(plan: Plan, signal, W, spectrum, scratch, stream=None):
+    """cwt_exec_with_power for a plan made with scratch="caller": its per-call
+    buffers are carved from ``scratch`` (a contiguous CUDA tensor of at least
+    cwt_plan_scratch_bytes bytes, 256 B aligned).  spectrum may be None."""
+    import torch
+    _check_signal(plan, signal)
+    _check_W(plan, W)
+    if spectrum is not None and (spectrum.dtype != torch.float64 or spectrum.numel() != plan.n_scales):
+        raise ValueError("spectrum must hold n_scales float64 values")
+    nbytes = scratch.numel() * scratch.element_size()
+    sp = _dev_ptr(spectrum, "spectrum") if spectrum is not None else None
+    _check(load_library().cwt_exec_scratch(plan._h, _dev_ptr(signal, "signal"), _dev_ptr(W, "W"), sp,
+                                           _dev_ptr(scratch, "scratch"), nbytes, _stream_ptr(stream)), plan)
     return W, spectrum
 
 

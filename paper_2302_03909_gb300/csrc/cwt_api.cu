@@ -441,6 +441,41 @@ cwt_status dev_alloc(cwt_plan* p, T** ptr, size_t count) {
     return CWT_OK;
 }
 
+// A per-call buffer: allocated with the plan, or (CWT_SCRATCH_CALLER) an
+// offset into the caller's scratch, bound by bind_scratch for each call.
+constexpr size_t kScratchAlign = 256;
+template <typename T>
+cwt_status scratch_alloc(cwt_plan* p, T** ptr, size_t count) {
+    if (p->opts.scratch != CWT_SCRATCH_CALLER) return dev_alloc(p, ptr, count);
+    *ptr = nullptr;
+    if (count == 0) return CWT_OK;
+    p->scratch_slots.push_back({reinterpret_cast<void**>(ptr), p->scratch_own});
+    p->scratch_own += (count * sizeof(T) + kScratchAlign - 1) / kScratchAlign * kScratchAlign;
+    return CWT_OK;
+}
+
+// bytes of scratch of a plan with its child and sub-plans
+size_t scratch_tree(const cwt_plan* p) {
+    size_t subs = 0;
+    for (const cwt_plan* q : p->subs) subs = std::max(subs, scratch_tree(q));
+    return p->scratch_own + (p->child ? scratch_tree(p->child) : 0) + subs;
+}
+
+// points every per-call buffer of the tree into base (nullptr: unbinds)
+void set_scratch(cwt_plan* p, char* base) {
+    for (const auto& sl : p->scratch_slots) {
+        void* a = base ? (void*)(base + sl.off) : nullptr;
+        std::memcpy(sl.ptr, &a, sizeof a);
+    }
+    size_t off = p->scratch_own;
+    if (p->child) {
+        set_scratch(p->child, base ? base + off : nullptr);
+        off += scratch_tree(p->child);
+    }
+    for (cwt_plan* q : p->subs) set_scratch(q, base ? base + off : nullptr);
+    p->scratch_base = base;
+}
+
 template <typename T>
 cwt_status upload(cwt_plan* p, T** ptr, const std::vector<T>& host) {
     cwt_status st = dev_alloc(p, ptr, host.size());
@@ -471,6 +506,7 @@ void free_plan(cwt_plan* p) {
     for (cudaEvent_t e : p->hc_ev) cudaEventDestroy(e);
     if (p->hc_stream) cudaStreamDestroy(p->hc_stream);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->opts.scratch == CWT_SCRATCH_CALLER) set_scratch(p, nullptr);   // not the plan's to free
     void* ptrs[] = {p->d_jobs, p->d_tile_job, p->d_part_off, p->d_part_cnt, p->d_Fp, p->d_Ft, p->d_Y,
                     p->d_partials, p->d_tw_lo, p->d_tw_hi, p->d_tw_tab, p->h_sig, p->h_W,
                     p->h_spec, p->d_pw_partials, p->d_env_part, p->d_env_cnt, p->d_icwt_coef};
@@ -504,6 +540,40 @@ EncodeTiledFn encode_tiled() {
         return (EncodeTiledFn)f;
     }();
     return fn;
+}
+bool enc_ok() { return encode_tiled() != nullptr; }
+
+// The tile pipeline's TMA map of Y as float rows: [slab][1024 rows][2 A floats];
+// boxes of 256 rows x 8 complex columns land in shared memory with the 64-byte
+// swizzle the kernels read
+cwt_status encode_ymap(cwt_plan* p) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const int64_t M = p->M, A = M >> p->wide_logl;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * A), 1024, (cuuint64_t)(p->y_count / (size_t)M)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(A * 8), (cuuint64_t)(M * 8)};
+    const cuuint32_t box[3] = {16, 256, 1}, estr[3] = {1, 1, 1};
+    if (enc(&p->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->d_Y, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return CWT_OK;
+}
+
+// binds a call's scratch to the plan tree (and encodes the TMA maps of Y at
+// their new addresses)
+cwt_status bind_scratch(cwt_plan* p, char* base) {
+    set_scratch(p, base);
+    cwt_status st = CWT_OK;
+    std::vector<cwt_plan*> todo{p};
+    while (!todo.empty() && st == CWT_OK) {
+        cwt_plan* q = todo.back();
+        todo.pop_back();
+        if (q->ymap_on) st = encode_ymap(q);
+        if (q->child) todo.push_back(q->child);
+        for (cwt_plan* r : q->subs) todo.push_back(r);
+    }
+    return st;
 }
 
 double out_row_bytes(const cwt_plan* p) {
@@ -747,32 +817,25 @@ cwt_status build_plan(cwt_plan* p) {
     if ((st = upload(p, &p->d_part_off, p->part_off)) != CWT_OK) return st;
     if ((st = upload(p, &p->d_part_cnt, p->part_cnt)) != CWT_OK) return st;
     if ((st = upload_twiddles(p)) != CWT_OK) return st;
-    if ((st = dev_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
-    if (!p->wide.empty() && (st = dev_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
+    if ((st = scratch_alloc(p, &p->d_Fp, (size_t)(M / 2 + 1))) != CWT_OK) return st;
+    if (!p->wide.empty() && (st = scratch_alloc(p, &p->d_Ft, (size_t)M)) != CWT_OK) return st;
     size_t ycount = 0;
     if (!small) ycount = (size_t)M;
     p->y_stride = (size_t)M * (size_t)std::max(1, std::min<int>(p->wide_G, (int)wide.size()));
     if (!p->wide.empty())
         ycount = std::max(ycount, p->y_stride * (size_t)std::min<size_t>(p->wide.size(), cwt_plan::kSide + 1));
-    if ((st = dev_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
+    if ((st = scratch_alloc(p, &p->d_Y, ycount)) != CWT_OK) return st;
+    p->y_count = ycount;
     if (!p->wide.empty() && wide2_on_tc(p)) {
-        // Y as float rows: [slab][1024 rows][2 A floats]; boxes of 256 rows x 8 complex
-        // columns land in shared memory with the 64-byte swizzle the kernel reads
-        EncodeTiledFn enc = encode_tiled();
-        if (!enc) return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        const int64_t A = M >> p->wide_logl;
-        const cuuint64_t dims[3] = {(cuuint64_t)(2 * A), 1024, (cuuint64_t)(ycount / (size_t)M)};
-        const cuuint64_t strides[2] = {(cuuint64_t)(A * 8), (cuuint64_t)(M * 8)};
-        const cuuint32_t box[3] = {16, 256, 1}, estr[3] = {1, 1, 1};
-        if (enc(&p->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p->d_Y, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        p->ymap_on = true;
+        if (!enc_ok()) return fail(p, CWT_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        // with caller scratch the map is encoded when a call binds its scratch
+        if (p->opts.scratch != CWT_SCRATCH_CALLER && (st = encode_ymap(p)) != CWT_OK) return st;
         CWT_CUDA(p, cudaHostAlloc((void**)&p->h_err, sizeof(int32_t), cudaHostAllocMapped));
         *p->h_err = 0;
         CWT_CUDA(p, cudaHostGetDevicePointer((void**)&p->d_err, p->h_err, 0));
     }
-    if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
+    if ((st = scratch_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return st;
     if (p->child) {
         std::vector<EdgeRow> er(p->child_n);
         std::vector<float2> h;
@@ -794,7 +857,7 @@ cwt_status build_plan(cwt_plan* p) {
         if ((st = upload(p, &d_er, er)) != CWT_OK) return st;
         p->d_edge_rows = d_er;
         if ((st = upload(p, &p->d_edge_h, h)) != CWT_OK) return st;
-        if ((st = dev_alloc(p, &p->d_edge_delta, (size_t)p->child_n * p->edge_bpr)) != CWT_OK) return st;
+        if ((st = scratch_alloc(p, &p->d_edge_delta, (size_t)p->child_n * p->edge_bpr)) != CWT_OK) return st;
     }
 
     // side streams and events, and the shared-memory opt-in of every kernel the
@@ -1380,6 +1443,11 @@ bool take_timeout(cwt_plan* p) {
 
 cwt_status run(cwt_plan* p, const void* signal, void* W, double* spectrum, cudaStream_t s) {
     if (take_timeout(p)) return fail(p, CWT_ERR_TIMEOUT, "a tensor-core pass 2 of an earlier call gave up waiting");
+    if (p->opts.scratch == CWT_SCRATCH_CALLER) {
+        // the scratch changes from call to call: no graph replay
+        if (!p->scratch_base) return fail(p, CWT_ERR_INVALID_ARG, "the plan runs with caller scratch (cwt_exec_scratch)");
+        return run_launches(p, signal, W, spectrum, s);
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (p->timing || p->hc.on || !p->graphs_ok || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread ||
         cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
@@ -1511,17 +1579,30 @@ cwt_status create_bluestein(cwt_plan** plan, int64_t N, const double* wt, int32_
     if ((st = upload(p, &p->d_part_cnt, p->part_cnt)) != CWT_OK) return bail(st);
     if ((st = upload_twiddles(p)) != CWT_OK) return bail(st);
     if ((st = upload(p, &p->d_bs_chirp, chirp)) != CWT_OK) return bail(st);
-    if ((st = dev_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return bail(st);
+    if ((st = scratch_alloc(p, &p->d_partials, (size_t)std::max<int64_t>(1, nparts))) != CWT_OK) return bail(st);
     if ((st = dev_alloc(p, &p->d_bs_G, (size_t)(2 * P))) != CWT_OK) return bail(st);
     p->bs_streams = std::min<int>((int)p->jobs.size(), cwt_plan::kSide + 1);
-    if ((st = dev_alloc(p, &p->d_bs_work, (size_t)(P + 2 * P * p->bs_streams))) != CWT_OK) return bail(st);
-    if (!p->fwd_small && (st = dev_alloc(p, &p->d_Y, (size_t)(P * p->bs_streams))) != CWT_OK) return bail(st);
+    if ((st = scratch_alloc(p, &p->d_bs_work, (size_t)(P + 2 * P * p->bs_streams))) != CWT_OK) return bail(st);
+    if (!p->fwd_small && (st = scratch_alloc(p, &p->d_Y, (size_t)(P * p->bs_streams))) != CWT_OK) return bail(st);
     if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return bail(CWT_ERR_CUDA);
     for (int i = 0; i < cwt_plan::kSide; i++)
         if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
             return bail(CWT_ERR_CUDA);
-    // D of the chirp sequences: [0] conj(c) (signal stage), [1] c (scales)
+    // D of the chirp sequences: [0] conj(c) (signal stage), [1] c (scales); a
+    // plan with caller scratch computes them in a temporary one
+    char* tmp = nullptr;
+    if (p->opts.scratch == CWT_SCRATCH_CALLER) {
+        const cudaError_t e = cudaMalloc((void**)&tmp, p->scratch_own);
+        if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : CWT_ERR_CUDA);
+        set_scratch(p, tmp);
+    }
+    struct TmpScratch {   // freed on every return (after the plan, on the error paths)
+        char* t;
+        ~TmpScratch() {
+            if (t) cudaFree(t);
+        }
+    } tmp_guard{tmp};
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(CWT_ERR_CUDA);
     const Params B = base_params(p);
@@ -1545,6 +1626,7 @@ cwt_status create_bluestein(cwt_plan** plan, int64_t N, const double* wt, int32_
     if (cudaStreamSynchronize(s) != cudaSuccess && st == CWT_OK) st = CWT_ERR_CUDA;
     cudaStreamDestroy(s);
     if (st != CWT_OK) return bail(st);
+    if (tmp) set_scratch(p, nullptr);
     *plan = p;
     return CWT_OK;
 }
@@ -1621,12 +1703,11 @@ cwt_status create_periodic_extended(cwt_plan** plan, int64_t N, const double* sc
     }
     p->logM = ilog2(p->M);
     const size_t se = o.input_dtype == CWT_INPUT_F64 ? sizeof(double) : sizeof(float);
-    cudaError_t e = cudaMalloc(&p->d_ext, (size_t)(N + 2 * p->ext_E) * se);
-    if (e != cudaSuccess) {
+    cwt_status st = scratch_alloc(p, reinterpret_cast<char**>(&p->d_ext), (size_t)(N + 2 * p->ext_E) * se);
+    if (st != CWT_OK) {
         free_plan(p);
-        return e == cudaErrorMemoryAllocation ? CWT_ERR_OOM : CWT_ERR_CUDA;
+        return st;
     }
-    p->ws_bytes += (size_t)(N + 2 * p->ext_E) * se;
     *plan = p;
     return CWT_OK;
 }
@@ -1970,7 +2051,7 @@ void cwt_plan_opts_default(cwt_plan_opts* o) {
     o->precision = CWT_PRECISION_FP32;
     o->band_depth = 0;
     o->wide2_kernel = 0;
-    o->reserved_ = 0;
+    o->scratch = CWT_SCRATCH_PLAN;
 }
 
 cwt_status cwt_plan_create(cwt_plan** plan, int64_t N, const double* scales, int32_t n_scales, int32_t wavelet,
@@ -2003,7 +2084,8 @@ cwt_status cwt_plan_create_ex(cwt_plan** plan, int64_t N, const double* scales, 
         o.precision < CWT_PRECISION_FP32 || o.precision > CWT_PRECISION_BF16X3 ||
         (o.band_depth != 0 && o.band_depth != 1 && o.band_depth != 2 && o.band_depth != 4 && o.band_depth != 8 &&
          o.band_depth != 16) ||
-        o.wide2_kernel < 0 || o.wide2_kernel > 2 || o.reserved_ != 0)
+        o.wide2_kernel < 0 || o.wide2_kernel > 2 || (o.scratch != CWT_SCRATCH_PLAN && o.scratch != CWT_SCRATCH_CALLER) ||
+        (o.scratch == CWT_SCRATCH_CALLER && o.tune != 0))
         return CWT_ERR_INVALID_ARG;
     if (o.tune) return create_tuned(plan, N, scales, n_scales, wavelet, boundary, o);
     if (o.min_ctas == 0) o.min_ctas = kMinCtas;
@@ -2135,6 +2217,27 @@ cwt_status cwt_exec_with_power(cwt_plan* plan, const void* signal_dev, void* W_d
     return run(plan, signal_dev, W_dev, spectrum_dev, (cudaStream_t)stream);
 }
 
+cwt_status cwt_plan_scratch_bytes(const cwt_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return CWT_ERR_INVALID_ARG;
+    *bytes = plan->opts.scratch == CWT_SCRATCH_CALLER ? scratch_tree(plan) : 0;
+    return CWT_OK;
+}
+
+cwt_status cwt_exec_scratch(cwt_plan* plan, const void* signal_dev, void* W_dev, double* spectrum_dev,
+                            void* scratch_dev, size_t scratch_bytes, void* stream) {
+    cwt_status st = check_exec_args(plan, signal_dev, W_dev);
+    if (st != CWT_OK) return st;
+    if (plan->opts.scratch != CWT_SCRATCH_CALLER)
+        return fail(plan, CWT_ERR_INVALID_ARG, "the plan has its own scratch (cwt_exec_with_power)");
+    if (spectrum_dev && !aligned(spectrum_dev, 8)) return fail(plan, CWT_ERR_INVALID_ARG, "bad spectrum pointer");
+    if (!scratch_dev || !aligned(scratch_dev, kScratchAlign) || scratch_bytes < scratch_tree(plan))
+        return fail(plan, CWT_ERR_INVALID_ARG, "scratch missing, misaligned or too small");
+    if ((st = bind_scratch(plan, (char*)scratch_dev)) == CWT_OK)
+        st = run(plan, signal_dev, W_dev, spectrum_dev, (cudaStream_t)stream);
+    set_scratch(plan, nullptr);
+    return st;
+}
+
 cwt_status cwt_wavelet_power(cwt_plan* plan, const void* W_dev, double* spectrum_dev, void* stream) {
     if (!plan) return CWT_ERR_INVALID_ARG;
     size_t we = plan->wavelet == CWT_WAVELET_MORLET ? 8 : 4;
@@ -2168,6 +2271,8 @@ cwt_status cwt_exec_host(cwt_plan* plan, const void* signal_host, void* W_host, 
                          void* stream) {
     if (!plan) return CWT_ERR_INVALID_ARG;
     if (!signal_host || !W_host) return fail(plan, CWT_ERR_INVALID_ARG, "null host pointer");
+    if (plan->opts.scratch == CWT_SCRATCH_CALLER)
+        return fail(plan, CWT_ERR_INVALID_ARG, "the plan runs with caller scratch (cwt_exec_scratch)");
     cwt_status st = check_device(plan);
     if (st != CWT_OK) return st;
     size_t se = plan->opts.input_dtype == CWT_INPUT_F64 ? 8 : 4;
@@ -2308,6 +2413,8 @@ cwt_status cwt_batch_create(cwt_batch** batch, cwt_plan* const* plans, const voi
         double* sp = spectra_dev ? spectra_dev[i] : nullptr;
         if (sp && !aligned(sp, 8)) return fail(p, CWT_ERR_INVALID_ARG, "bad spectrum pointer");
         if (p->timing) return fail(p, CWT_ERR_INVALID_ARG, "timing is on: a batch records the plan's launches");
+        if (p->opts.scratch == CWT_SCRATCH_CALLER)
+            return fail(p, CWT_ERR_INVALID_ARG, "a plan with caller scratch cannot join a batch");
     }
     // 1. record every plan's launch sequence with its dependency levels; the
     //    plan's own pointer stands for the call's stream (never passed to CUDA)

@@ -67,6 +67,7 @@ struct cwt_plan {
     std::vector<WideBatch> wide;          // wide jobs, in L2-sized batches
     int wide_logl = 0, wide_loga = 0, wide_G = 0;
     size_t y_stride = 0;                  // elements of Y per stream
+    size_t y_count = 0;                   // elements of Y (all streams)
     int fwd_small = 0;
     int crop = 0;                         // N < M: drop the padded outputs
     int64_t n_partials = 0;
@@ -163,6 +164,16 @@ struct cwt_plan {
     void* d_ext = nullptr;                // N + 2 ext_E samples, the input's dtype
 
     Recorder* rec = nullptr;              // set while a batch records this plan's launches
+
+    // caller-supplied scratch (opts.scratch = CWT_SCRATCH_CALLER): each per-call
+    // buffer is an offset into the call's scratch.  This plan's own buffers lie
+    // in [0, scratch_own); the child plan's tree follows; the sub-plans' trees
+    // follow that, all at one offset (they run one after another).
+    struct ScratchSlot { void** ptr; size_t off; };
+    std::vector<ScratchSlot> scratch_slots;
+    size_t scratch_own = 0;
+    char* scratch_base = nullptr;         // bound for the duration of one call
+    bool ymap_on = false;                 // the tile pipeline's TMA map of Y is in use
 
     // tensor-core pass 2 (opts.precision != FP32, L = 1024): TMA map of Y, and a
     // flag in mapped host memory that its kernel sets when a bounded wait gives up

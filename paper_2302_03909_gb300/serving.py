@@ -301,7 +301,7 @@ class Server:
     def __init__(self, budget_bytes: int, slots: int = 4, plan_cache_bytes: Optional[int] = None,
                  keep_results: bool = False, device: int = 0, reuse_buffers: bool = True,
                  reuse_max_bytes: int = 64 << 20, policy: str = "fifo", max_wait_s: float = 0.25,
-                 plan_opts: Optional[dict] = None):
+                 plan_opts: Optional[dict] = None, caller_scratch: bool = True):
         import torch
 
         import paper_2302_03909_gb300 as cwt
@@ -313,6 +313,11 @@ class Server:
         # 500 requests/s, same served rate)
         self.plan_opts = {"wide2_kernel": 2} if plan_opts is None else dict(plan_opts)
         self.dev = torch.device("cuda", device)
+        # shapes whose requests get new buffers also get their plan's per-call
+        # scratch per request (cwt_exec_scratch): the cached instance then holds
+        # its tables only, so many such shapes stay resident
+        self.caller_scratch = caller_scratch
+        self.scratch_known: Dict[tuple, int] = {}
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
         self.reuse = reuse_buffers
         self.reuse_max = reuse_max_bytes
@@ -324,11 +329,17 @@ class Server:
         self.in_flight: List[tuple] = []      # (req, slot, bytes, plan, event, tensors)
         self.completed: List[Request] = []
 
+    def _uses_caller_scratch(self, key) -> bool:
+        return self.caller_scratch and not self._owns_buffers(Request(-1, *key, 0.0))
+
     def _make_plan(self, key):
         torch = self.torch
         N, scales, wavelet, boundary = key
+        opts = dict(self.plan_opts)
+        if self._uses_caller_scratch(key):
+            opts["scratch"] = "caller"
         try:
-            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary, **self.plan_opts)
+            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary, **opts)
         except self.cwt.CwtError as e:
             # device memory that torch's caching allocator holds (freed request
             # buffers) is not visible to the library's allocations: release it
@@ -337,7 +348,9 @@ class Server:
                 raise
             torch.cuda.synchronize(self.dev)
             torch.cuda.empty_cache()
-            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary, **self.plan_opts)
+            p = self.cwt.cwt_plan_create(N, np.asarray(scales), wavelet, boundary, **opts)
+        p._scratch = self.cwt.cwt_plan_scratch_bytes(p) if opts.get("scratch") == "caller" else 0
+        self.scratch_known[key] = p._scratch
         p._io, p._io_bytes = None, 0
         if self._owns_buffers(Request(-1, *key, 0.0)):
             p._io = (torch.empty(N, dtype=torch.float32, device=self.dev), p.empty_output(self.dev),
@@ -355,8 +368,12 @@ class Server:
     def _own_bytes(self, req: Request) -> int:
         # requests that run in their instance's buffers need nothing of their
         # own, unless their result is kept (a copy); the instance (workspace
-        # and buffers) is charged by the ledger
-        return req.io_bytes if (not self._owns_buffers(req) or self.keep) else 0
+        # and buffers) is charged by the ledger.  A request with caller scratch
+        # also holds its plan's scratch (bounded until the plan exists).
+        own = req.io_bytes if (not self._owns_buffers(req) or self.keep) else 0
+        if self._uses_caller_scratch(req.key):
+            own += self.scratch_known.get(req.key, workspace_bound(req.N, req.scales, req.wavelet, req.boundary))
+        return own
 
     def submit(self, req: Request):
         self.ledger.submit(req)
@@ -372,20 +389,26 @@ class Server:
                 W = plan.empty_output(self.dev)
                 sp = torch.empty(plan.n_scales, dtype=torch.float64, device=self.dev)
             sig.copy_(req.signal, non_blocking=True)
-            self.cwt.cwt_exec_with_power(plan, sig, W, sp, st)
+            scratch = None
+            if getattr(plan, "_scratch", 0):
+                scratch = torch.empty(plan._scratch, dtype=torch.uint8, device=self.dev)
+                self.cwt.cwt_exec_scratch(plan, sig, W, sp, scratch, st)
+            else:
+                self.cwt.cwt_exec_with_power(plan, sig, W, sp, st)
             if self.keep and plan._io is not None:
                 W, sp = W.clone(), sp.clone()
             ev = torch.cuda.Event()
             ev.record(st)
         req.t_admit = now
-        self.in_flight.append((req, slot, nbytes, plan, ev, (sig, W, sp)))
+        # the scratch stays referenced until the request completes
+        self.in_flight.append((req, slot, nbytes, plan, ev, (sig, W, sp, scratch)))
 
     def poll(self, now: float) -> int:
         """Retires finished requests and admits queued ones; returns the number retired."""
         n = 0
         still = []
         for item in self.in_flight:
-            req, slot, nbytes, plan, ev, (sig, W, sp) = item
+            req, slot, nbytes, plan, ev, (sig, W, sp, _) = item
             if ev.query():
                 req.t_done = now
                 if self.keep:

@@ -80,6 +80,7 @@ def test_paper_grid_matches_sec_3_1(cwt):
     (dict(N=64, scales=[2.0], band_depth=32), 1),
     (dict(N=64, scales=[2.0], wide2_kernel=3), 1),
     (dict(N=64, scales=[2.0], wide2_kernel=-1), 1),
+    (dict(N=64, scales=[2.0], scratch="caller", tune=True), 1),     # a tuned plan runs itself
 ])
 def test_plan_argument_checks(cwt, kwargs, status):
     kw = dict(kwargs)
@@ -113,6 +114,14 @@ def test_batch_and_options_entry_points_check_their_arguments(cwt):
     assert lib.cwt_batch_info(None, None, None, None, None) == 1
     assert lib.cwt_batch_destroy(None) == 0
     assert lib.cwt_plan_get_opts(None, None) == 1
+    n = ctypes.c_size_t()
+    assert lib.cwt_plan_scratch_bytes(None, ctypes.byref(n)) == 1
+    o = cwt._Opts()
+    lib.cwt_plan_opts_default(ctypes.byref(o))
+    o.scratch = 2                                                  # neither cwt_scratch_mode
+    sc = (ctypes.c_double * 1)(2.0)
+    assert lib.cwt_plan_create_ex(ctypes.byref(h), 64, sc, 1, 0, 0, ctypes.byref(o)) == 1
+    assert lib.cwt_exec_scratch(None, None, None, None, None, 0, None) == 1
     with pytest.raises(ValueError):
         cwt.cwt_batch_create([])
 
@@ -125,7 +134,7 @@ def test_plan_options_struct_matches_the_header(cwt):
     assert ctypes.sizeof(o) == 72
     assert (o.omega0, o.dx, o.scale_unit, o.input_dtype, o.fft_len) == (6.0, 1.0, 0, 0, 0)
     assert (o.eps_trunc, o.min_ctas, o.tune, o.wide_batch_bytes) == (1e-10, 0, 0, 0)
-    assert (o.precision, o.band_depth, o.wide2_kernel, o.reserved_) == (0, 0, 0, 0)
+    assert (o.precision, o.band_depth, o.wide2_kernel, o.scratch) == (0, 0, 0, 0)
     with open(os.path.join(ROOT, "include", "cwt.h")) as fh:
         text = fh.read()
     body = text[text.index("typedef struct {", text.index("cwt_input_dtype;")):text.index("} cwt_plan_opts;")]

@@ -209,6 +209,7 @@ def test_plan_creation_retries_once_after_releasing_the_torch_cache():
 
     srv = serving.Server.__new__(serving.Server)
     srv.torch, srv.dev, srv.reuse, srv.plan_opts = FakeTorch, None, False, {"wide2_kernel": 2}
+    srv.caller_scratch, srv.scratch_known = False, {}
     key = (1024, (2.0, 4.0), "gdw", "periodic")
     srv.cwt = make_cwt(1)
     p = srv._make_plan(key)
