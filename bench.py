@@ -81,7 +81,7 @@ def parse_args():
     # serving: a Poisson trace of requests through paper_2302_03909_gb300.serving
     ap.add_argument("--serving", action="store_true", help="measure request latency instead of throughput")
     ap.add_argument("--rate", type=float, default=500.0, help="serving: requests per second")
-    ap.add_argument("--serving-lengths", default="pow2", choices=["integer", "pow2"],
+    ap.add_argument("--serving-lengths", default="integer", choices=["integer", "pow2"],
                     help="serving: signal lengths log-uniform integers (2 per octave) or powers of two")
     ap.add_argument("--seconds", type=float, default=5.0, help="serving: length of the arrival trace")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests in flight at once")
