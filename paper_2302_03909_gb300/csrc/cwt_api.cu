@@ -625,6 +625,47 @@ const Entry& wide2_entry(const cwt_plan* p) { return tables().wide2[p->wide_logl
 
 cwt_status opt_in_smem(cwt_plan* p, const void* fn);
 
+// CTAs of kernel fn (nt threads, smem bytes of shared memory) the device holds
+// at once; 0 when unknown
+int64_t resident_ctas(cwt_plan* p, const void* fn, int nt, size_t smem, int* sms_out) {
+    int sms = 0, n = 0;
+    *sms_out = 0;
+    if (!fn || opt_in_smem(p, fn) != CWT_OK) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    *sms_out = sms;
+    return (int64_t)n * sms;
+}
+
+// Tiles per CTA of a W-writing launch of njobs jobs of tiles_job tiles each
+// (ceil(tiles_job / D) CTAs per job), given the CTAs the device holds at once
+// (slots): the D in 1..kMaxD with the shortest makespan in tile times,
+// ceil(CTAs / slots) x (D + kCtaSetup), among those keeping at least min_ctas
+// CTAs (or all of the launch's tiles); ties go to the larger D.  A launch whose
+// CTAs fill a whole number of waves then ends together instead of leaving a
+// part-empty last wave.  Plans asking for fewer CTAs than SMs (made for
+// batches, whose grouped launches merge many plans) keep pick_D's largest D.
+constexpr double kCtaSetup = 0.5;          // a CTA's set-up (band values, job), in tile times
+int pick_D_waves(int64_t tiles_job, int64_t njobs, int min_ctas, int64_t slots, int sms) {
+    if (slots <= 0 || min_ctas < sms) return pick_D(tiles_job * njobs, min_ctas);
+    const int64_t floor_ctas = std::min<int64_t>(min_ctas, tiles_job * njobs);
+    int best = 1;
+    double best_t = 1e300;
+    for (int d = 1; d <= kMaxD; d++) {
+        const int64_t ctas = njobs * ((tiles_job + d - 1) / d);
+        if (ctas < floor_ctas) break;      // a larger D has no more CTAs
+        const double t = (double)((ctas + slots - 1) / slots) * ((double)d + kCtaSetup);
+        if (t <= best_t) {
+            best_t = t;
+            best = d;
+        }
+    }
+    return best;
+}
+
 // twiddle tables of length p->M (FP64 generated, FP32 stored): the two-level
 // e^{-2 pi i j / M} and the stage tables e^{-2 pi i i / L}, L <= kLmax
 cwt_status upload_twiddles(cwt_plan* p) {
@@ -731,7 +772,12 @@ cwt_status build_plan(cwt_plan* p) {
         const int64_t A = M >> ll;
         const int T = tb.band[ll][0].T;
         const int64_t tiles_job = (A + T - 1) / T;
-        const int D = pick_D(tiles_job * (int64_t)by_logl[slot].size(), p->opts.min_ctas);
+        const int crop = p->N < M ? 1 : 0;
+        const Entry& be = g.rdi ? tb.band_rd[g.rdi][crop] : tb.band[ll][crop];
+        int sms = 0;
+        const int64_t slots = resident_ctas(p, (const void*)be.fn, be.NT,
+                                            (size_t)((1 << g.rdi) << ll) * sizeof(float2) + stage_smem(ll, be.T), &sms);
+        const int D = pick_D_waves(tiles_job, (int64_t)by_logl[slot].size(), p->opts.min_ctas, slots, sms);
         const int per_job = (int)((tiles_job + D - 1) / D);
         g.D = D;
         g.ntiles = 0;
@@ -794,7 +840,10 @@ cwt_status build_plan(cwt_plan* p) {
                 const int64_t per = std::max<int64_t>(1, sms / wb.count);
                 wb.D = (int)((tiles_job + per - 1) / per);
             } else {
-                wb.D = pick_D(tiles_job * wb.count, p->opts.min_ctas);
+                const Entry& e2 = tb.wide2[p->wide_logl][p->N < M ? 1 : 0];
+                int sms2 = 0;
+                const int64_t slots = resident_ctas(p, (const void*)e2.fn, e2.NT, stage_smem(p->wide_logl, e2.T), &sms2);
+                wb.D = pick_D_waves(tiles_job, wb.count, p->opts.min_ctas, slots, sms2);
             }
         }
         for (size_t i = 0; i < wide.size(); i++) {
@@ -1842,7 +1891,7 @@ cwt_status create_zero_split(cwt_plan** plan, int64_t N, const double* scales, i
 // appended after tuning, so a later process skips the timing.
 namespace {
 
-constexpr uint64_t kTuneVersion = 3;   // 3: pass-2 kernel chosen per plan, per-batch pass-2 grids
+constexpr uint64_t kTuneVersion = 4;   // 4: wave-aware tiles per CTA; 3: pass-2 kernel per plan, per-batch pass-2 grids
 
 uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
     const unsigned char* b = (const unsigned char*)data;
