@@ -14,7 +14,7 @@ def test_traffic_scales_with_the_launch_size():
     half = bench.load_traffic("wide2", "lognormal_n4m_s128", 67108864.0)
     assert full is not None and abs(full - 216036096.0) < 1.0
     assert abs(half - full / 2) < 1.0
-    assert bench.load_traffic("band", "lognormal_n4m_s128", 1.0) is None
+    assert bench.load_traffic("forward", "lognormal_n4m_s128", 1.0) is None
     # no capture of the current pass-2 kernel on this workload: no traffic figure
     assert bench.load_traffic("wide2", "lognormal_n1m_morlet_s64", 26.0e6) is None
     assert bench.load_traffic("wide2", "no_such_workload", 1.0) is None
