@@ -182,7 +182,8 @@ cwt_status cwt_plan_get_opts(const cwt_plan* plan, cwt_plan_opts* opts);
 cwt_status cwt_plan_destroy(cwt_plan* plan);
 
 /* M (the largest transform length for a plan whose N is not a power of two),
- * the plan's device workspace in bytes, and whether W is complex
+ * the plan's device workspace in bytes (for a CWT_SCRATCH_CALLER plan its
+ * tables only; see cwt_plan_scratch_bytes), and whether W is complex
  * (1: interleaved complex64, Morlet; 0: float32, the real wavelets).  Any out-pointer may be NULL. */
 cwt_status cwt_plan_info(const cwt_plan* plan, int64_t* fft_len, size_t* workspace_bytes,
                          int32_t* out_is_complex);
