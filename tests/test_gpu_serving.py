@@ -34,6 +34,36 @@ def test_served_results_equal_standalone():
     srv.close()
 
 
+def test_served_with_caller_scratch_equals_standalone():
+    """Integer lengths (most not powers of two) and no buffers owned by plan
+    instances: every request runs its plan with caller scratch
+    (cwt_exec_scratch, a scratch per request) and still equals, bit for bit,
+    a plan with its own scratch run alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_03909_gb300 as cwt
+    from paper_2302_03909_gb300 import serving
+    trace = serving.poisson_trace(2000.0, 0.02, seed=12, log2n=(10, 16), n_scales=(8, 24), integer_lengths=2)
+    assert len(trace) >= 20 and any(r.N & (r.N - 1) for r in trace)
+    sig = {}
+    for r in trace:
+        if r.N not in sig:
+            sig[r.N] = torch.tensor(synth.lognormal_field(r.N, seed=r.N), dtype=torch.float32).pin_memory()
+        r.signal = sig[r.N]
+    srv = serving.Server(budget_bytes=4 << 30, slots=4, keep_results=True, reuse_max_bytes=0)
+    stats = serving.run_trace(srv, trace, max_seconds=120.0)
+    assert stats["requests"] == len(trace)
+    assert all(v > 0 for v in srv.scratch_known.values())
+    for r in srv.completed:
+        plan = cwt.cwt_plan_create(r.N, np.asarray(r.scales), r.wavelet, r.boundary)
+        W, sp = cwt.cwt_exec_with_power(plan, r.signal.cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(W, r.W) and torch.equal(sp, r.spectrum), r.rid
+        plan.close()
+    srv.close()
+
+
 def test_batch_graph_equals_direct_calls():
     """A batch of uneven lengths (periodic lengths that are not powers of two
     included) captured as one CUDA graph and replayed gives the same W and
