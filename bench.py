@@ -81,13 +81,15 @@ def parse_args():
     # serving: a Poisson trace of requests through paper_2302_03909_gb300.serving
     ap.add_argument("--serving", action="store_true", help="measure request latency instead of throughput")
     ap.add_argument("--rate", type=float, default=500.0, help="serving: requests per second")
+    ap.add_argument("--max-wait", type=float, default=0.1,
+                    help="serving, smallest-first policy: a request older than this (s) goes first")
     ap.add_argument("--serving-lengths", default="integer", choices=["integer", "pow2"],
                     help="serving: signal lengths log-uniform integers (2 per octave) or powers of two")
     ap.add_argument("--seconds", type=float, default=5.0, help="serving: length of the arrival trace")
     ap.add_argument("--slots", type=int, default=4, help="serving: requests in flight at once")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device-memory budget")
     ap.add_argument("--policy", default="smallest", choices=["fifo", "smallest"],
-                    help="serving: admission order of the concurrent run (smallest first, 0.25 s maximum wait)")
+                    help="serving: admission order of the concurrent run (smallest first, 0.1 s maximum wait by default)")
     ap.add_argument("--fresh-buffers", action="store_true",
                     help="serving: new device buffers per request (direct launches) instead of per-instance buffers")
     # batching: many signals of uneven lengths, each with its own plan
@@ -434,7 +436,7 @@ def run_serving(args, embedded=False):
                                  ("serial", 1, "fifo")):
         for r in trace:
             r.t_admit = r.t_done = float("nan")
-        srv = serving.Server(budget, slots=slots, plan_cache_bytes=budget // 2,
+        srv = serving.Server(budget, slots=slots, plan_cache_bytes=budget // 2, max_wait_s=args.max_wait,
                              reuse_buffers=not args.fresh_buffers, policy=policy)
         keys = sorted({r.key for r in trace})
         for k in keys:                                       # resident plans
@@ -458,7 +460,8 @@ def run_serving(args, embedded=False):
             "offered_scale_samples_per_s": mean_units * len(trace) / args.seconds,
             "concurrent": out["concurrent"], "concurrent_fifo": out["concurrent_fifo"], "serial": out["serial"],
             "config": {"rate_per_s": args.rate, "seconds": args.seconds, "requests": len(trace),
-                       "slots": args.slots, "policy": args.policy, "budget_gb": args.budget_gb,
+                       "slots": args.slots, "policy": args.policy, "max_wait_s": args.max_wait,
+                       "budget_gb": args.budget_gb,
                        "N": ("log-uniform integers in 2^10..2^24 (a pool of 2 per octave, mostly not powers "
                              "of two)" if per_octave else "2^10..2^24 (powers of two)"),
                        "distinct_shapes": len({r.key for r in trace}),

@@ -159,7 +159,7 @@ class Admission:
     """Admission against a byte budget and a number of slots ("fifo" or
     "smallest" first with a maximum wait)."""
 
-    def __init__(self, budget_bytes: int, slots: int, policy: str = "fifo", max_wait_s: float = 0.25):
+    def __init__(self, budget_bytes: int, slots: int, policy: str = "fifo", max_wait_s: float = 0.1):
         if policy not in ("fifo", "smallest"):
             raise ValueError(policy)
         self.budget, self.slots = budget_bytes, slots
@@ -243,7 +243,7 @@ class Ledger:
     ``bound(request)`` until it exists and its size is known."""
 
     def __init__(self, budget_bytes: int, slots: int, cache: "PlanCache", own_bytes: Callable[[Request], int],
-                 policy: str = "fifo", max_wait_s: float = 0.25,
+                 policy: str = "fifo", max_wait_s: float = 0.1,
                  bound: Callable[[Request], int] = lambda r: workspace_bound(r.N, r.scales, r.wavelet, r.boundary)):
         self.adm = Admission(budget_bytes, slots, policy, max_wait_s)
         self.cache, self.own_bytes, self.bound = cache, own_bytes, bound
@@ -300,7 +300,7 @@ class Server:
 
     def __init__(self, budget_bytes: int, slots: int = 4, plan_cache_bytes: Optional[int] = None,
                  keep_results: bool = False, device: int = 0, reuse_buffers: bool = True,
-                 reuse_max_bytes: int = 64 << 20, policy: str = "fifo", max_wait_s: float = 0.25,
+                 reuse_max_bytes: int = 64 << 20, policy: str = "fifo", max_wait_s: float = 0.1,
                  plan_opts: Optional[dict] = None, caller_scratch: bool = True):
         import torch
 
