@@ -43,6 +43,7 @@ constexpr size_t kWideBatchBytesTc = size_t(128) << 20;
 // grid at >= kMinCtas CTAs (two per SM: the band value table and the job set-up
 // are paid once per CTA), at most kMaxD
 constexpr int kMaxD = 8;
+constexpr int kPackMinLog = 4;             // real-input forward by the M/2-point packed form from M = 16
 constexpr int kMinCtas = 152 * 2;
 int pick_D(int64_t tiles_total, int min_ctas) {
     int64_t d = tiles_total / min_ctas;
@@ -409,6 +410,46 @@ static __global__ void k_periodic_extend_g(GroupMap g) {
     Cta c;
     const ExtendArgs& a = group_args<ExtendArgs>(g, c);
     periodic_extend_body(a, c);
+}
+
+// Forward transform of a real signal (Params::fpack): the forward passes leave
+// Z, the M/2-point e^{-} DFT of z(q) = f(2q) + i f(2q + 1), in F[0 .. M/2).
+// The DFTs of the even and odd samples are E(k) = (Z(k) + conj Z(-k)) / 2 and
+// O(k) = (Z(k) - conj Z(-k)) / (2i) (indices mod M/2), the e^{-} DFT of f is
+// X(k) = E(k) + e^{-2 pi i k / M} O(k), and F(k) = conj X(k) for k <= M/2 (the
+// paper's e^{+} sign, Eq. 8).  One thread takes the pair (k, M/2 - k): both
+// outputs read the same two values, so the pass runs in place.
+struct UntangleArgs {
+    float2* F;
+    const float2* tw_lo;
+    const float2* tw_hi;
+    int64_t M;
+    int32_t h, pad_;
+};
+// conj(E + w O) from za = Z(a), zb = Z(-a), w = e^{-2 pi i a / M}
+__device__ __forceinline__ float2 untangle_one(float2 za, float2 zb, float2 w) {
+    const float2 e = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+    const float2 o = make_float2(0.5f * (za.y + zb.y), -0.5f * (za.x - zb.x));
+    return make_float2(e.x + (w.x * o.x - w.y * o.y), -(e.y + (w.x * o.y + w.y * o.x)));
+}
+__device__ __forceinline__ float2 untangle_tw(const UntangleArgs& a, int64_t j) {
+    const float2 hi = __ldg(&a.tw_hi[j >> a.h]), lo = __ldg(&a.tw_lo[j & ((int64_t(1) << a.h) - 1)]);
+    return make_float2(hi.x * lo.x - hi.y * lo.y, hi.x * lo.y + hi.y * lo.x);
+}
+__device__ __forceinline__ void untangle_body(const UntangleArgs& a, const Cta c) {
+    const int64_t half = a.M >> 1;
+    for (int64_t k = c.x * (int64_t)blockDim.x + threadIdx.x; k <= (half >> 1); k += (int64_t)c.nx * blockDim.x) {
+        const int64_t kp = half - k;
+        const float2 zk = a.F[k], zkp = a.F[kp == half ? 0 : kp];
+        a.F[k] = untangle_one(zk, zkp, untangle_tw(a, k));
+        a.F[kp] = untangle_one(zkp, zk, untangle_tw(a, kp));
+    }
+}
+static __global__ void k_fwd_untangle(UntangleArgs a) { untangle_body(a, cta_plain()); }
+static __global__ void k_fwd_untangle_g(GroupMap g) {
+    Cta c;
+    const UntangleArgs& a = group_args<UntangleArgs>(g, c);
+    untangle_body(a, c);
 }
 
 // ====================================================================== plan
@@ -1069,6 +1110,42 @@ cwt_status check_device(cwt_plan* p) {
 cwt_status launch_forward(cwt_plan* p, const Params& P, cudaStream_t fs, double in_bytes, double out_bytes) {
     const Tables& tb = tables();
     cwt_status st;
+    // a real signal: the M/2-point DFT of its samples packed in pairs, then the
+    // untangle pass (k_fwd_untangle); complex inputs (P.cin) take the M-point form
+    if (!P.cin && P.cmode == 0 && p->logM >= kPackMinLog) {
+        Params Q = P;
+        Q.fpack = 1;
+        Q.cmode = 3;                                  // the passes write Z whole
+        const int lmt = p->logM - 1;
+        if (lmt <= kLmaxLog) {
+            Q.A = 1;
+            st = launch(p, tb.fwd_small[lmt], dim3(1), stage_smem(lmt, 1), Q, fs, CWT_KCLASS_FORWARD, in_bytes);
+        } else {
+            const Entry& e1 = tb.fwd1[p->wide_loga - 1];
+            const int L = 1 << p->wide_logl;
+            st = launch(p, e1, dim3((L + e1.T - 1) / e1.T), stage_smem(p->wide_loga - 1, e1.T), Q, fs,
+                        CWT_KCLASS_FORWARD, in_bytes);
+            if (st == CWT_OK) {
+                const Entry& e2 = tb.fwd2[p->wide_logl];
+                Q.A = (int32_t)((p->M >> 1) >> p->wide_logl);
+                st = launch(p, e2, dim3((Q.A + e2.T - 1) / e2.T), stage_smem(p->wide_logl, e2.T), Q, fs,
+                            CWT_KCLASS_FORWARD, 0.0);
+            }
+        }
+        if (st != CWT_OK) return st;
+        const int64_t pairs = (p->M >> 2) + 1;
+        const unsigned blocks = (unsigned)std::min<int64_t>(4096, (pairs + 255) / 256);
+        const UntangleArgs a{P.Fp_out, p->d_tw_lo, p->d_tw_hi, p->M, p->h, 0};
+        if (p->rec) {
+            rec_launch(p, (const void*)k_fwd_untangle_g, dim3(blocks), dim3(256), 0, fs, a);
+            return CWT_OK;
+        }
+        LaunchTimer lt(p, CWT_KCLASS_FORWARD, out_bytes, fs);
+        k_fwd_untangle<<<blocks, 256, 0, fs>>>(a);
+        CWT_CUDA(p, cudaGetLastError());
+        lt.done();
+        return CWT_OK;
+    }
     if (p->fwd_small) {
         const Entry& e = tb.fwd_small[p->logM];
         Params Q = P;

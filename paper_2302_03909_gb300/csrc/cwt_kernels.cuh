@@ -98,7 +98,7 @@ struct Params {
     const float2* cin;
     const float2* cG;
     int32_t cmode;
-    int32_t pad2_;
+    int32_t fpack;           // forward: 1 = real input packed as f(2q) + i f(2q + 1), an M/2-point DFT
 };
 
 // Rows of the wide-scale intermediate in the order the tensor-core pass 2
@@ -704,9 +704,11 @@ struct YOut {
         const uint64_t pol = l2_policy_keep();
         const uint32_t dj = d1 + (uint32_t)A1 * (uint32_t)j;
         constexpr int CH = R >= 8 ? 4 : 1;                 // interleaved recurrences
-        const float2 g = tw_m(*p, (b * (uint32_t)A1 * (uint32_t)stride) & mask);
+        // e^{-2 pi i b d / Mt} for the transform length Mt = M >> fpack, from the M table
+        const uint32_t sh = (uint32_t)p->fpack;
+        const float2 g = tw_m(*p, ((b * (uint32_t)A1 * (uint32_t)stride) << sh) & mask);
         float2 w[CH];
-        w[0] = tw_m(*p, (b * dj) & mask);
+        w[0] = tw_m(*p, ((b * dj) << sh) & mask);
 #pragma unroll
         for (int c = 1; c < CH; c++) w[c] = cmul(w[c - 1], g);
         float2 gc = g;
@@ -854,6 +856,12 @@ struct SigFill {
         if (p->cin) {
 #pragma unroll
             for (int r = 0; r < R; r++) v[r] = __ldg(&p->cin[b0 + t + L * (j + r * stride)]);
+        } else if (p->fpack) {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int q = b0 + t + L * (j + r * stride);
+                v[r] = make_float2(load_signal(*p, 2 * q), load_signal(*p, 2 * q + 1));
+            }
         } else {
 #pragma unroll
             for (int r = 0; r < R; r++) v[r] = make_float2(load_signal(*p, b0 + t + L * (j + r * stride)), 0.f);
@@ -892,7 +900,7 @@ template <int LOGA, int T, int MAXLR>
 __device__ __forceinline__ void fwd1_body(const Params& p, const Cta c) {
     constexpr int NT = T * col_threads(LOGA, MAXLR);
     extern __shared__ float2 smem[];
-    const int L = p.M >> LOGA;
+    const int L = (p.M >> p.fpack) >> LOGA;
     const int b0 = c.x * T;
     SigFill fill{&p, b0, L};
     YOut<true> out{&p, p.Y, b0, 0, 1 << LOGA, 1};
