@@ -224,3 +224,63 @@ def test_plan_creation_retries_once_after_releasing_the_torch_cache():
     with pytest.raises(cwt.CwtError):
         srv._make_plan(key)
     assert calls == {"create": 1, "empty": 0}
+
+
+def test_integer_length_pool_and_trace():
+    """Two integer lengths per octave, log-uniform in each, the top power of two
+    included; a trace drawn from the pool is reproducible and spans it."""
+    pool = serving.length_pool((10, 24), per_octave=2, seed=5)
+    assert pool == sorted(set(pool)) and pool[-1] == 1 << 24
+    for u in range(10, 24):
+        assert 1 <= sum((1 << u) <= n < (1 << (u + 1)) for n in pool) <= 2
+    assert sum(n & (n - 1) == 0 for n in pool) <= 2          # mostly not powers of two
+    t1 = serving.poisson_trace(500.0, 2.0, seed=3, integer_lengths=2)
+    t2 = serving.poisson_trace(500.0, 2.0, seed=3, integer_lengths=2)
+    assert [(r.N, r.scales, r.wavelet, r.boundary, r.t_arrival) for r in t1] == \
+           [(r.N, r.scales, r.wavelet, r.boundary, r.t_arrival) for r in t2]
+    full = set(serving.length_pool((10, 24), per_octave=2))
+    assert {r.N for r in t1} <= full and len({r.N for r in t1}) > len(full) // 2
+    assert all(r.scales[0] == 4.0 and abs(r.scales[-1] - max(8.0, r.N / 4)) < 1e-6 * r.N for r in t1)
+
+
+def test_caller_scratch_is_charged_to_the_request():
+    """A shape whose requests bring new buffers gets a caller-scratch plan: the
+    ledger charges the request its scratch (a bound until the plan exists, then
+    the plan's own figure) and the cached instance its tables only, so the
+    bytes counted never exceed the budget."""
+    import paper_2302_03909_gb300 as cwt
+
+    class ScratchPlan(FakePlan):
+        pass
+
+    made = []
+
+    class FakeCwt:
+        CwtError = cwt.CwtError
+
+        @staticmethod
+        def cwt_plan_create(N, scales, wavelet, boundary, **opts):
+            p = ScratchPlan((N, tuple(scales), wavelet, boundary), 1000 if opts.get("scratch") == "caller" else 10**6)
+            p.opts = opts
+            made.append(p)
+            return p
+
+        @staticmethod
+        def cwt_plan_scratch_bytes(p):
+            return 5000
+
+    srv = serving.Server.__new__(serving.Server)
+    srv.torch, srv.dev, srv.cwt = None, None, FakeCwt
+    srv.reuse, srv.reuse_max, srv.keep, srv.plan_opts = True, 64 << 20, False, {"wide2_kernel": 2}
+    srv.caller_scratch, srv.scratch_known = True, {}
+    big = serving.Request(0, 1 << 22, tuple(np.geomspace(4.0, 1 << 20, 32)), "morlet", "zero", 0.0)
+    small = serving.Request(1, 1 << 10, (4.0, 8.0), "gdw", "periodic", 0.0)
+    assert srv._uses_caller_scratch(big.key) and not srv._uses_caller_scratch(small.key)
+    bound = serving.workspace_bound(big.N, big.scales, big.wavelet, big.boundary)
+    assert srv._own_bytes(big) == big.io_bytes + bound         # before the plan exists
+    p = srv._make_plan(big.key)
+    assert p.opts == {"wide2_kernel": 2, "scratch": "caller"} and p._scratch == 5000
+    assert srv._own_bytes(big) == big.io_bytes + 5000           # the plan's own figure
+    assert srv._size_of(p) == 1000                              # tables only in the cache
+    srv.caller_scratch = False
+    assert srv._own_bytes(big) == big.io_bytes
