@@ -10,7 +10,10 @@ at the stated padded length M).
 * Zero boundary, any N: any padded length M' >= N + E + 1 gives the first N
   outputs of the M = pow2 >= 2N transform.
 
-Each needs the dilated wavelet to be short (negligible beyond E samples) and
+* The forward transform of a real signal from the half-length transform of
+  its samples packed in pairs (this one needs no condition).
+
+Each of the first three needs the dilated wavelet to be short (negligible beyond E samples) and
 its spectrum to be negligible at the Nyquist frequency; the last test shows
 an identity failing where the second condition does not hold.
 """
@@ -129,3 +132,33 @@ def test_a_spectrum_cut_at_nyquist_breaks_the_identities(orc):
     W = orc.cwt_fft(f, [s], "morlet", M=pow2_at_least(2 * N), omega0=OMEGA0)[0]
     Wp = orc.cwt_fft(f, [s], "morlet", M=pow2_at_least(N + support("morlet", s) + 1), omega0=OMEGA0)[0]
     assert rel(Wp, W) > 1e-5
+
+
+@pytest.mark.parametrize("M,N", [(16, 16), (64, 40), (1024, 1000), (4096, 1537), (1 << 14, 1 << 13)])
+def test_real_forward_from_the_half_length_packed_transform(orc, M, N):
+    """The GPU path forms the forward transform of a real signal (Eq. 8, the
+    e^{+} sign) from the M/2-point transform Z of z(q) = f(2q) + i f(2q + 1):
+    F(k) = conj(E(k) + e^{-2 pi i k/M} O(k)), E(k) = (Z(k) + conj Z(-k)) / 2,
+    O(k) = (Z(k) - conj Z(-k)) / (2i), k <= M/2, indices of Z mod M/2.
+    Checked here with the oracle's own FFT, and the in-place pairing
+    (k, M/2 - k) the kernel uses."""
+    f = np.zeros(M)
+    f[:N] = synth.lognormal_field(N, seed=M + N)
+    h = M // 2
+    F_ref = orc.fft(f.astype(complex), sign=+1)[:h + 1]          # sum_n f(n) e^{+2 pi i k n / M}
+    Z = orc.fft(f[0::2] + 1j * f[1::2], sign=-1)
+    buf = np.zeros(h + 1, complex)
+    buf[:h] = Z
+
+    def one(a, za, zb):
+        E = (za + np.conj(zb)) / 2
+        O = (za - np.conj(zb)) / 2j
+        return np.conj(E + np.exp(-2j * np.pi * a / M) * O)
+    for k in range(h // 2 + 1):
+        kp = h - k
+        zk, zkp = buf[k], buf[kp % h]
+        buf[k], buf[kp] = one(k, zk, zkp), one(kp, zkp, zk)
+    assert np.max(np.abs(buf - F_ref)) < 1e-12 * np.max(np.abs(F_ref))
+    # a mistake in the pairing (Z(-k) taken as Z(k)) fails
+    bad = np.conj((Z[:h] + np.conj(Z[:h])) / 2 + np.exp(-2j * np.pi * np.arange(h) / M) * (Z[:h] - np.conj(Z[:h])) / 2j)
+    assert np.max(np.abs(bad - F_ref[:h])) > 1e-3 * np.max(np.abs(F_ref))
