@@ -29,11 +29,16 @@ The loop has three parts:
   instead of a launch sequence, which is what small requests are dominated
   by.  Larger shapes get new buffers per request: their launch cost is small
   against their run time, and instances holding their W would crowd the plan
-  cache.  A result the server keeps is copied out of the instance's W on the
-  request's stream.
+  cache.  Their plans are made with caller scratch (``scratch="caller"``):
+  the cached instance keeps its constant tables only, and each request takes
+  the plan's per-call buffers from torch's allocator for its own lifetime
+  (``cwt_exec_scratch``), charged to the request.  Many shapes then stay
+  resident at once.  A result the server keeps is copied out of the
+  instance's W on the request's stream.
 
 ``run_trace`` replays a timed arrival trace (open loop) and reports latency
-percentiles; ``poisson_trace`` draws the arrivals.  Both the admission and
+percentiles; ``poisson_trace`` draws the arrivals, with power-of-two lengths
+or log-uniform integer lengths from ``length_pool``.  Both the admission and
 the cache are plain host logic, tested on CPU with fakes.
 """
 from __future__ import annotations
